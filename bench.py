@@ -1,0 +1,392 @@
+"""Benchmark: GLUPS of the two-component D3Q19 Shan-Chen step on GB300.
+
+Default workload: spinodal mixture on a 256^3 periodic grid (tau = 1,
+G = 0.65, rho_A = 0.5 + 0.05 U(-1,1) seed 1234, rho_B = 1 - rho_A, u = 0),
+FP32 populations, fused kernel; FP16/BF16 deviation storage and the two-pass
+kernel are timed beside it. GLUPS = nx*ny*nz / (1e9 * seconds per step)
+(Eq. glups). The state (2 x 2.55 GB at 256^3 FP32) is far larger than the
+129 MB L2, so no flush is needed between steps.
+
+One JSON line on rank 0. ``--impl reference`` times the FP64 CPU oracle on
+the host cores instead (bounded sample of the same workload). With N > 1
+(torchrun) every rank runs an independent replica (the single lattice is not
+decomposed across GPUs), and value = all site updates / max-over-ranks time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GLUPS, 2-comp D3Q19 Shan-Chen 256^3, FP32 vs FP16-store; % of HBM roofline"
+BYTES_PER_SITE = {"fp32": 304, "fp16": 152, "bf16": 152}   # 38 pops read + written once
+DTYPE_TAG = {"fp32": "f32", "fp16": "f16-store/f32-compute", "bf16": "bf16-store/f32-compute"}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_per_site(prec):
+    """Per-site DRAM bytes of the fused kernel from the committed ncu summary
+    (dram__bytes_read.sum + dram__bytes_write.sum per launch / sites)."""
+    p = os.path.join(ROOT, "profiles", "fused_step_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    for line in open(p):
+        parts = line.split()
+        if len(parts) >= 2 and parts[0] == prec and not line.startswith("#"):
+            return float(parts[1])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def workload(name, grid=None):
+    from paper_2112_08264_gb300 import inputs
+    if name == "spinodal256":
+        n = grid or 256
+        rA, rB = inputs.spinodal(n, n, n, seed=1234)
+        return dict(shape=(n, n, n), tau=1.0, G=0.65, rA=rA, rB=rB, mask=None,
+                    desc="spinodal %d^3 periodic, tau=1, G=0.65, rho_A=0.5+0.05U(-1,1) seed 1234" % n)
+    if name == "colloid256":
+        n = 256
+        rA, rB = inputs.spinodal(n, n, n, seed=1234)
+        mask, _ = inputs.colloid_mask(n, n, n, n_spheres=4000, radius=5.0, seed=4321)
+        return dict(shape=(n, n, n), tau=1.0, G=0.65, rA=rA, rB=rB, mask=mask,
+                    desc="256^3, 4000 static spheres R=5 (seed 4321), halfway bounce-back")
+    if name == "spinodal512":
+        n = 512
+        rA, rB = inputs.spinodal(n, n, n, seed=1234)
+        return dict(shape=(n, n, n), tau=1.0, G=0.65, rA=rA, rB=rB, mask=None,
+                    desc="spinodal 512^3 periodic, tau=1, G=0.65")
+    raise ValueError(name)
+
+
+def time_device(W, prec, kernel, steps, warmup, events_per_step=False):
+    """Device-resident timing: inputs already in HBM; CUDA events on the
+    solver's stream around exactly `steps` steps."""
+    import torch
+    from paper_2112_08264_gb300 import Solver
+    nx, ny, nz = W["shape"]
+    s = Solver(nx, ny, nz, W["tau"], W["G"], mask=W["mask"], prec=prec, kernel=kernel)
+    dA = torch.tensor(W["rA"], dtype=torch.float32, device="cuda")
+    dB = torch.tensor(W["rB"], dtype=torch.float32, device="cuda")
+    s.init(dA, dB)
+    del dA, dB
+    s.step(warmup)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(s.stream):
+        e0.record(s.stream)
+        s.step(steps)
+        e1.record(s.stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    info = s.launch_info()
+    st = s.stats()
+    s.close()
+    torch.cuda.synchronize()
+    return ms, info, st
+
+
+def time_e2e(W, prec, kernel, steps):
+    """End to end through the public API from HOST arrays: pinned H2D of the
+    initial fields, init, `steps` steps, moments, D2H of rho_A, rho_B, u."""
+    import torch
+    from paper_2112_08264_gb300 import Solver, run_host
+    nx, ny, nz = W["shape"]
+    s = Solver(nx, ny, nz, W["tau"], W["G"], mask=W["mask"], prec=prec, kernel=kernel)
+    rA = W["rA"].astype(np.float32)
+    rB = W["rB"].astype(np.float32)
+    run_host(rA, rB, 3, W["tau"], W["G"], solver=s)      # warm
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    (oA, oB, ou), _ = run_host(rA, rB, steps, W["tau"], W["G"], solver=s)
+    t1 = time.perf_counter()
+    s.close()
+    n = nx * ny * nz
+    h2d = 2 * n * 4
+    d2h = 5 * n * 4
+    return t1 - t0, h2d, d2h, bool(np.isfinite(oA).all())
+
+
+def oracle_sample(shape, tau, G, budget_s, min_steps=1, max_steps=1000, per_step_budget=None):
+    """Time the FP64 oracle on a periodic slab of the workload (full x-y
+    plane, nz_s planes) sized so the run takes about budget_s seconds."""
+    import oracle
+    from paper_2112_08264_gb300 import inputs
+    nx, ny, nz = shape
+    cores = oracle.max_threads()
+    oracle.set_threads(cores)
+    # probe the speed on a thin slab
+    rA, rB = inputs.spinodal(nx, ny, 2, seed=1234)
+    f = oracle.init(rA, rB)
+    t0 = time.perf_counter()
+    oracle.step(f, tau, G)
+    rate = nx * ny * 2 / max(time.perf_counter() - t0, 1e-6)   # sites/s
+    if per_step_budget is not None:
+        nzs = int(max(1, min(nz, per_step_budget * rate / (nx * ny))))
+        steps = None
+    else:
+        nzs = int(max(2, min(nz, 16)))
+        steps = int(max(min_steps, min(max_steps, budget_s * rate / (nx * ny * nzs))))
+    rA, rB = inputs.spinodal(nx, ny, nzs, seed=1234)
+    return rA, rB, nzs, steps, cores
+
+
+def run_cpu_baseline(W, budget_s=15.0):
+    import oracle
+    nx, ny, nz = W["shape"]
+    rA, rB, nzs, steps, cores = oracle_sample(W["shape"], W["tau"], W["G"], budget_s)
+    f = oracle.init(rA, rB)
+    t0 = time.perf_counter()
+    oracle.run(f, steps, W["tau"], W["G"])
+    dt = time.perf_counter() - t0
+    glups = nx * ny * nzs * steps / dt / 1e9
+    return {"value": glups, "unit": "GLUPS", "cores": cores, "kind": "oracle",
+            "sample": "%d FP64 oracle steps on a %dx%dx%d periodic slab of the workload (%.1f s)"
+                      % (steps, nx, ny, nzs, dt)}
+
+
+def clocks_ok(c):
+    bad = {"hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"}
+    if any(r in bad for r in c.get("reasons", [])):
+        return False
+    if c.get("sm_mhz") and c.get("sm_max_mhz") and c["sm_mhz"] < 0.5 * c["sm_max_mhz"] \
+            and "sw_power_cap" not in c.get("reasons", []):
+        return False
+    return True
+
+
+def main_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    W = workload(args.config, args.grid)
+    nx, ny, nz = W["shape"]
+    import oracle
+    # each step a bounded slab sample sized so warmup + steps take ~150 s
+    per_step = 150.0 / max(1, args.steps + args.warmup)
+    rA, rB, nzs, _, cores = oracle_sample(W["shape"], W["tau"], W["G"], None, per_step_budget=per_step)
+    f = oracle.init(rA, rB)
+    for _ in range(args.warmup):
+        f = oracle.step(f, W["tau"], W["G"])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f = oracle.step(f, W["tau"], W["G"])
+    dt = time.perf_counter() - t0
+    glups = nx * ny * nzs * args.steps / dt / 1e9
+    sample = "each step: one FP64 oracle step on a %dx%dx%d periodic slab of the workload" % (nx, ny, nzs)
+    line = {"impl": "reference", "metric": METRIC, "value": glups, "unit": "GLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": W["desc"], "sample": sample},
+            "cpu_baseline": {"value": glups, "unit": "GLUPS", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": glups, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="spinodal256", choices=["spinodal256", "colloid256", "spinodal512"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--kernel", default="fused", choices=["fused", "two_pass"])
+    ap.add_argument("--grid", type=int, default=None, help="override the spinodal grid size (profiling)")
+    ap.add_argument("--no-variants", action="store_true", help="skip the FP16/BF16/two-pass lines")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return main_reference(args, world, rank)
+
+    import torch
+    from paper_2112_08264_gb300 import build
+    if rank == 0 or world > 1:
+        build.build()
+    W = workload(args.config, args.grid)
+    nx, ny, nz = W["shape"]
+    N = nx * ny * nz
+    peak, peak_kind = measured_peaks()
+
+    barrier(world)
+    with ClockSampler(local) as clk:
+        ms, info, st = time_device(W, args.prec, args.kernel, args.steps, args.warmup)
+    clocks = clk.summary()
+    if not clocks_ok(clocks):
+        with ClockSampler(local) as clk:
+            ms, info, st = time_device(W, args.prec, args.kernel, args.steps, args.warmup)
+        clocks = clk.summary()
+        clocks["remeasured"] = True
+    barrier(world)
+    ms_max = max_over_ranks(ms, world)
+    step_s = ms_max / 1e3 / args.steps
+    glups = world * N / step_s / 1e9
+
+    bps = BYTES_PER_SITE[args.prec]
+    if W["mask"] is not None:
+        fluid = float((W["mask"] == 0).mean())
+        alg_bytes = fluid * bps + 4          # populations of fluid nodes + 4-byte flag word
+    else:
+        fluid = 1.0
+        alg_bytes = bps
+    kernel_s = (ms / 1e3) / (args.steps * info["launches_per_step"])
+    achieved = alg_bytes * N / kernel_s / 1e9 if info["launches_per_step"] == 1 else \
+        alg_bytes * N / (ms / 1e3 / args.steps) / 1e9
+    tps = traffic_per_site(args.prec) if (args.kernel == "fused" and W["mask"] is None) else None
+
+    line = {
+        "metric": METRIC, "value": glups, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": DTYPE_TAG[args.prec], "data": "synthetic",
+        "config": {"workload": W["desc"], "grid": [nx, ny, nz], "prec": args.prec, "kernel": args.kernel,
+                   "parallelism": "replicas" if world > 1 else "single-gpu",
+                   "l2": "state %.2f GB per buffer > 129 MB L2; no flush needed" % (38 * N * (bps / 76) / 1e9),
+                   "launch": info},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_site": alg_bytes,
+                     "traffic": (tps * N if tps is not None else None)},
+        "gpu_launches": args.steps * info["launches_per_step"],
+        "clocks": clocks,
+        "conserved_totals": [float(x) for x in st],
+    }
+    if rank == 0 and not args.no_e2e:
+        dt, h2d, d2h, ok = time_e2e(W, args.prec, args.kernel, args.steps)
+        line["e2e"] = {"value": N * args.steps / dt / 1e9, "unit": "GLUPS",
+                       "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+                       "what": "host arrays -> pinned H2D -> lb_init -> %d steps -> moments -> D2H" % args.steps}
+    if rank == 0 and not args.no_variants:
+        var = {}
+        for prec, kern in (("fp16", "fused"), ("bf16", "fused"), ("fp32", "two_pass")):
+            if (prec, kern) == (args.prec, args.kernel):
+                continue
+            vms, vinfo, _ = time_device(W, prec, kern, args.steps, args.warmup)
+            vstep = vms / 1e3 / args.steps
+            vb = BYTES_PER_SITE[prec] * (fluid if W["mask"] is not None else 1.0)
+            var["%s_%s" % (prec, kern)] = {"GLUPS": N / vstep / 1e9, "ms_per_step": vstep * 1e3,
+                                          "hbm_frac_of_%s" % peak_kind: vb * N / vstep / 1e9 / peak,
+                                          "launches_per_step": vinfo["launches_per_step"]}
+        line["variants"] = var
+        if "fp16_fused" in var and args.prec == "fp32":
+            line["fp16_over_fp32"] = var["fp16_fused"]["GLUPS"] / glups
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = run_cpu_baseline(W)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,175 @@
+/*
+ * lb.h -- C ABI of the GB300 two-component D3Q19 lattice-Boltzmann library.
+ *
+ * The library advances two immiscible fluid components A and B on an
+ * nx*ny*nz D3Q19 lattice (Sec. 2 Method: 19 velocities, rest + 6 at distance
+ * 1 + 12 at distance sqrt 2) with BGK relaxation (Eq. bgk), the second-order
+ * equilibrium (Eq. LEQ), streaming along c_i (Eq. bgk, left-hand side),
+ * periodic wrap and halfway bounce-back at solid links for walls at rest
+ * (Eq. LADDFLBE with u_b = 0; interior solid nodes hold no fluid, Sec. 2).
+ * Components interact through a Shan-Chen pseudopotential force with
+ * psi = rho, which the paper does not give (its two-component model is the
+ * colour-gradient one); the library uses the standard form of the LBM text
+ * the paper cites (Krueger et al. 2017):
+ *     F^A(x) = -G psi^A(x) sum_{i=1..18} w_i psi^B(x + c_i) c_i,
+ * F^B likewise with A and B swapped, psi = 0 on solid nodes, the lattice
+ * weights w_i = 1/18, 1/36 as force weights, plus an optional body force
+ * rho^k g. The force enters through the original Shan-Chen velocity shift:
+ * u' = sum_k sum_i c_i f_i^k / sum_k rho^k (one relaxation time), and
+ * component k relaxes to f^eq(rho^k, u' + tau F^k / rho^k).
+ *
+ * Conventions shared by every entry point:
+ *   - Site index s = x + nx*(y + ny*z): x fastest, as the paper's column-major
+ *     layout with x contiguous (Sec. 3 Implementation, Sec. 4).
+ *   - Velocity order (public): 0 rest; 1..6 = +x, -x, +y, -y, +z, -z;
+ *     7..18 = (+1,+1,0), (-1,-1,0), (+1,-1,0), (-1,+1,0), (+1,0,+1),
+ *     (-1,0,-1), (+1,0,-1), (-1,0,+1), (0,+1,+1), (0,-1,-1), (0,+1,-1),
+ *     (0,-1,+1); the opposite of an odd i is i + 1.
+ *   - Population arrays are [k][i][s], k = 0 (A), 1 (B): 2*19*N floats. The
+ *     state exchanged through the ABI is the post-streaming, pre-collision f.
+ *   - Field pointers whose name starts with d_ are DEVICE pointers on the
+ *     current device, caller-owned, contiguous, N = nx*ny*nz elements in
+ *     site order (velocities: SoA, 3*N, component a at a*N + s).
+ *   - The library never allocates device memory: every buffer it needs is a
+ *     slice of the caller's workspace (lb_workspace_bytes tells its size).
+ *   - All device work runs on the stream given at lb_create (or lb_set_stream),
+ *     in order. Calls documented as synchronous wait for that stream.
+ *   - Errors are returned as lb_status values; nothing throws across the ABI.
+ *     A CUDA error becomes LB_ECUDA and lb_last_error() gives its text.
+ *   - A context is not thread-safe: one host thread at a time per context.
+ */
+#ifndef LB_H
+#define LB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lb_ctx lb_ctx;
+
+typedef enum {
+    LB_OK = 0,
+    LB_EINVAL = 1,      /* invalid argument */
+    LB_ENOMEM = 2,      /* caller workspace too small */
+    LB_ECUDA = 3,       /* CUDA error (text: lb_last_error) */
+    LB_ENONFINITE = 4,  /* a non-finite population was found */
+    LB_ESTATE = 5,      /* call not valid in the context's state */
+    LB_ETIMEOUT = 6     /* a bounded device wait gave up */
+} lb_status;
+
+/* Storage of the populations. All three compute in FP32. The stored value is
+ * the deviation d_i^k = f_i^k - w_i rho0^k from the rest equilibrium at the
+ * base densities rho0^k, rounded to nearest-even for the 16-bit forms. */
+typedef enum { LB_FP32 = 0, LB_FP16_DEV = 1, LB_BF16_DEV = 2 } lb_precision;
+
+/* Time-stepping kernel. FUSED: one pass per step (pull streaming, densities
+ * of the tile and its halo on chip, force, collision, store) -- the paper's
+ * fused approach (Sec. 5.1). TWO_PASS: a density pass then a
+ * stream + force + collide pass -- the paper's plain approach. */
+typedef enum { LB_KERNEL_FUSED = 0, LB_KERNEL_TWO_PASS = 1 } lb_kernel;
+
+typedef struct {
+    int prec;              /* lb_precision (default LB_FP32) */
+    int kernel;            /* lb_kernel (default LB_KERNEL_FUSED) */
+    double rho0_A, rho0_B; /* deviation base; <= 0 means: the fluid-site mean of
+                              the densities given to lb_init */
+    double body_force[3];  /* g, added as rho^k g to F^k (default 0) */
+    int ckpt_every;        /* K > 0: lb_step records a checkpoint every K steps
+                              for lb_backward; 0 = no recording (default) */
+    int ckpt_steps_max;    /* longest recorded run, in steps (needed when K > 0) */
+} lb_options;
+
+/* Fill *opt with the defaults above. */
+void lb_default_options(lb_options* opt);
+
+/* Bytes of device workspace lb_create needs for this grid and options
+ * (two population buffers, density scratch, reduction scratch, the solid
+ * flags when a mask is used -- counted always -- and, when
+ * opt->ckpt_every > 0, checkpoints plus the adjoint's buffers). opt may be
+ * NULL (defaults). Returns 0 for invalid sizes. Pure host function. */
+size_t lb_workspace_bytes(int nx, int ny, int nz, const lb_options* opt);
+
+/* Create a context over the caller's workspace.
+ *   nx, ny, nz  >= 3 each, nx*ny*nz < 2^31.
+ *   tau         > 0.5 (positive viscosity, Eq. viscosity), finite.
+ *   G           finite Shan-Chen coupling (G > 0 repels A from B).
+ *   mask        HOST pointer to N bytes, 1 = solid node, 0 = fluid; NULL =
+ *               all fluid (periodic box). Copied; the caller keeps ownership.
+ *   opt         NULL = defaults.
+ *   d_workspace device pointer, 256-byte aligned, ws_bytes >= lb_workspace_bytes.
+ *   stream      a cudaStream_t (NULL = the legacy default stream).
+ * Errors: LB_EINVAL for bad sizes/parameters/alignment, LB_ENOMEM for a short
+ * workspace, LB_ECUDA. Synchronous (the mask upload waits). */
+lb_status lb_create(int nx, int ny, int nz, float tau, float G, const uint8_t* mask,
+                    const lb_options* opt, void* d_workspace, size_t ws_bytes,
+                    void* stream, lb_ctx** out);
+
+/* Set the stream used by all later calls on this context. */
+lb_status lb_set_stream(lb_ctx* ctx, void* stream);
+
+/* Initial state f_i^k = f_i^eq(rho^k, u) (Eq. LEQ) at every fluid node, from
+ * device fields d_rhoA, d_rhoB (N floats) and d_u (3N floats SoA, or NULL
+ * for u = 0). Resets the step counter and any recording. LB_EINVAL if a
+ * fluid node has rho^k <= 0 or a non-finite input (the force shift divides
+ * by rho^k). Synchronous. */
+lb_status lb_init(lb_ctx* ctx, const float* d_rhoA, const float* d_rhoB, const float* d_u);
+
+/* Advance n >= 1 time steps (Eq. bgk with the force shift, then streaming
+ * with bounce-back). Asynchronous on the context stream. When recording
+ * (ckpt_every > 0) LB_ESTATE if the run would exceed ckpt_steps_max. */
+lb_status lb_step(lb_ctx* ctx, int n);
+
+/* Moments of the current state into device fields: rho^A, rho^B (N floats
+ * each, 0 at solid nodes) and, when d_u != NULL, the mixture velocity
+ * u = (sum_k sum_i c_i f_i^k + (F^A + F^B)/2) / (rho^A + rho^B) (3N floats
+ * SoA, 0 at solid nodes). Any output pointer may be NULL. Asynchronous. */
+lb_status lb_moments(lb_ctx* ctx, float* d_rhoA, float* d_rhoB, float* d_u);
+
+/* Conserved totals over fluid nodes, accumulated in FP64: out5 = {sum rho^A,
+ * sum rho^B, sum_k sum_i c_i f_i^k (x, y, z)}. out5 is a HOST pointer.
+ * LB_ENONFINITE if any population is not finite. Synchronous. */
+lb_status lb_stats(lb_ctx* ctx, double out5[5]);
+
+/* Copy the current state (post-streaming f, [k][i][s], 2*19*N floats, 0 at
+ * solid nodes) to / from device memory. Asynchronous. lb_set_state does not
+ * change the step counter or the recording. */
+lb_status lb_get_state(lb_ctx* ctx, float* d_dst);
+lb_status lb_set_state(lb_ctx* ctx, const float* d_src);
+
+/* Steps taken since lb_init. */
+long long lb_steps_done(const lb_ctx* ctx);
+
+/* Reverse-mode gradient of a loss of the final densities of a recorded run
+ * (lb_init, then lb_step calls with ckpt_every = K > 0).
+ *   d_dL_drhoA, d_dL_drhoB  device fields (N floats) dL/drho^k(final); either
+ *                           may be NULL (= 0).
+ *   d_grad_rhoA0, d_grad_rhoB0  device outputs (N floats, may be NULL):
+ *                           dL/drho^k of the fields given to lb_init (u = 0
+ *                           treated as a constant).
+ *   grad_G                  HOST pointer to one double (may be NULL): dL/dG.
+ * Recomputes each K-step segment from its checkpoint, then runs the adjoint
+ * step backwards through it. LB_ESTATE without a recorded run. Synchronous.
+ * The context's state is restored to the final state afterwards. */
+lb_status lb_backward(lb_ctx* ctx, const float* d_dL_drhoA, const float* d_dL_drhoB,
+                      float* d_grad_rhoA0, float* d_grad_rhoB0, double* grad_G);
+
+/* Launch geometry the fused step uses (for measurement): number of kernel
+ * launches per lb_step(1), and the tile/grid shape chosen at lb_create. */
+lb_status lb_launch_info(const lb_ctx* ctx, int* launches_per_step, int* grid_blocks,
+                         int* block_threads, int* z_split);
+
+/* Destroy the context (does not free the caller's workspace). NULL is a no-op. */
+void lb_destroy(lb_ctx* ctx);
+
+/* Static text for a status; text of the last CUDA error seen by the calling
+ * thread ("" if none). */
+const char* lb_status_str(lb_status s);
+const char* lb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LB_H */

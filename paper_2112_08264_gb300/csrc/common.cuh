@@ -1,0 +1,173 @@
+// common.cuh -- per-site building blocks shared by the step, moment and
+// reduction kernels.
+//
+// State in device memory: the POST-COLLISION populations g of the last step,
+// stored as deviations d = g - w_i rho0^k, [k][i][s]. One step is then a pull
+// (Sec. 3 one-step two-grid scheme, two buffers, read one / write the other):
+//   f_i(x) = g_i(x - c_i)         if x - c_i is fluid   (streaming, Eq. bgk)
+//   f_i(x) = g_opp(i)(x)          if x - c_i is solid   (halfway bounce-back at
+//                                                        rest, Eq. LADDFLBE)
+// followed by densities, the Shan-Chen force, the velocity shift and BGK
+// collision (Eq. bgk, Eq. LEQ), and a store of g(x).
+#pragma once
+#include <cstdint>
+#include "lattice.cuh"
+#include "store.cuh"
+
+namespace lbgb {
+
+struct Geom {
+    int nx, ny, nz;
+    int plane;       // nx * ny
+    long long N;     // sites; population (k, i) starts at (k * 19 + i) * N
+};
+
+struct Phys {
+    float tau;       // relaxation time
+    float omega;     // 1 / tau
+    float G;         // Shan-Chen coupling
+    float g[3];      // body force
+    float rho0[2];   // deviation base of components A, B
+};
+
+// solid-site flags: bit 0 = this node is solid; bit i (1..18) = node x - c_i
+// is solid (so f_i(x) comes from bounce-back).
+constexpr uint32_t kSolid = 1u;
+
+__device__ __forceinline__ int wrap_dec(int a, int n) { return a == 0 ? n - 1 : a - 1; }
+__device__ __forceinline__ int wrap_inc(int a, int n) { return a == n - 1 ? 0 : a + 1; }
+
+// Site indices of the pull sources x - c_i for the 19 velocities.
+struct PullIdx {
+    int own;
+    int src[Q];
+};
+
+__device__ __forceinline__ void pull_indices(const Geom& g, int x, int y, int z, PullIdx& P) {
+    const int xm = wrap_dec(x, g.nx), xp = wrap_inc(x, g.nx);
+    const int ym = wrap_dec(y, g.ny), yp = wrap_inc(y, g.ny);
+    const int zm = wrap_dec(z, g.nz), zp = wrap_inc(z, g.nz);
+    P.own = x + g.nx * (y + g.ny * z);
+    static_for<0, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        // source = x - c_i
+        const int sx = Vel<i>::x == 1 ? xm : (Vel<i>::x == -1 ? xp : x);
+        const int sy = Vel<i>::y == 1 ? ym : (Vel<i>::y == -1 ? yp : y);
+        const int sz = Vel<i>::z == 1 ? zm : (Vel<i>::z == -1 ? zp : z);
+        P.src[i] = sx + g.nx * (sy + g.ny * sz);
+    });
+}
+
+// Pull the 38 deviations of node P.own into d[k][i].
+template <typename S, bool MASK>
+__device__ __forceinline__ void pull(const S* __restrict__ src, const Geom& g, const PullIdx& P,
+                                     uint32_t flags, float (&d)[2][Q]) {
+    static_for<0, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        int idx = P.src[i];
+        int pop = i;
+        if constexpr (MASK && i != 0) {
+            if (flags & (1u << i)) { idx = P.own; pop = Vel<i>::opp; }
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+            d[k][i] = Store<S>::ld(src + (size_t)(k * Q + pop) * (size_t)g.N + (size_t)idx);
+    });
+}
+
+__device__ __forceinline__ float dens_sum(const float (&d)[Q]) {
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) s += d[i];
+    return s;
+}
+
+// Density deviations drho^k = rho^k - rho0^k = sum_i d_i^k and momentum
+// j = sum_k sum_i c_i d_i^k (sum_i c_i w_i rho0 = 0, so the deviations carry
+// the whole momentum). The momentum is summed over opposite pairs,
+// c_i (d_i - d_opp(i)), whose differences are exact when the two are close.
+__device__ __forceinline__ void sums(const float (&d)[2][Q], float& dA, float& dB, float (&j)[3]) {
+    dA = dens_sum(d[0]);
+    dB = dens_sum(d[1]);
+    j[0] = j[1] = j[2] = 0.f;
+    static_for<0, 9>([&](auto M) {
+        constexpr int i = 2 * decltype(M)::value + 1;   // (i, i + 1) are opposite
+        const float diff = (d[0][i] - d[0][i + 1]) + (d[1][i] - d[1][i + 1]);
+        if constexpr (Vel<i>::x != 0) j[0] += Vel<i>::x * diff;
+        if constexpr (Vel<i>::y != 0) j[1] += Vel<i>::y * diff;
+        if constexpr (Vel<i>::z != 0) j[2] += Vel<i>::z * diff;
+    });
+}
+
+// BGK collision with the Shan-Chen velocity shift, in deviation form, and
+// store of the post-collision node.
+//   SA, SB: sum_{i>=1} w_i psi^k(x + c_i) c_i for k = A, B.
+// F^A = -G psi^A SB + rho^A g, so tau F^A / rho^A = tau (-G SB + g) at a
+// fluid node (psi = rho there).
+// Equilibrium deviation: f^eq_i - w_i rho0 = w_i [(rho - rho0) + rho (3 c.u
+// + 4.5 (c.u)^2 - 1.5 u.u)] (Eq. LEQ with c_s^2 = 1/3).
+template <typename S>
+__device__ __forceinline__ void collide_store(const float (&d)[2][Q], const Phys& p, float dA, float dB,
+                                              const float (&j)[3], const float (&SA)[3],
+                                              const float (&SB)[3], S* __restrict__ dst,
+                                              const Geom& g, int own) {
+    const float rA = p.rho0[0] + dA, rB = p.rho0[1] + dB;
+    const float inv = 1.0f / (rA + rB);
+    const float up[3] = {j[0] * inv, j[1] * inv, j[2] * inv};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float (&Sk)[3] = (k == 0) ? SB : SA;
+        const float rk = (k == 0) ? rA : rB;
+        const float drk = (k == 0) ? dA : dB;
+        float u[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) u[a] = up[a] + p.tau * (p.g[a] - p.G * Sk[a]);
+        const float uu15 = 1.5f * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        static_for<0, Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            float cu = 0.f;
+            if constexpr (Vel<i>::x != 0) cu += Vel<i>::x * u[0];
+            if constexpr (Vel<i>::y != 0) cu += Vel<i>::y * u[1];
+            if constexpr (Vel<i>::z != 0) cu += Vel<i>::z * u[2];
+            const float deq = wgt<i>() * (drk + rk * (cu * (3.0f + 4.5f * cu) - uu15));
+            const float out = d[k][i] - p.omega * (d[k][i] - deq);
+            Store<S>::st(dst + (size_t)(k * Q + i) * (size_t)g.N + (size_t)own, out);
+        });
+    }
+}
+
+// Density deviations dpsi^k = psi^k - rho0^k of node (x, y, z): sum_i d_i^k at
+// a fluid node, -rho0^k at a solid node (psi = 0 there). Since
+// sum_{i>=1} w_i c_i = 0, the force sums S^k = sum_i w_i psi^k(x + c_i) c_i are
+// the same sums over dpsi, without the rounding of rho0 + sum_i d_i.
+template <typename S, bool MASK>
+__device__ __forceinline__ float2 density_at(const S* __restrict__ src, const uint32_t* __restrict__ flags,
+                                             const Geom& g, const Phys& p, int x, int y, int z) {
+    PullIdx P;
+    pull_indices(g, x, y, z, P);
+    uint32_t fl = 0;
+    if constexpr (MASK) {
+        fl = __ldg(flags + P.own);
+        if (fl & kSolid) return make_float2(-p.rho0[0], -p.rho0[1]);
+    }
+    float d[2][Q];
+    pull<S, MASK>(src, g, P, fl, d);
+    return make_float2(dens_sum(d[0]), dens_sum(d[1]));
+}
+
+// S^k = sum_{i>=1} w_i psi^k(x + c_i) c_i from a lookup of dpsi(dx, dy, dz).
+template <typename Look>
+__device__ __forceinline__ void neighbour_sums(Look&& psi, float (&SA)[3], float (&SB)[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) SA[a] = SB[a] = 0.f;
+    static_for<1, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        const float2 v = psi(Vel<i>::x, Vel<i>::y, Vel<i>::z);
+        constexpr float w = wgt<i>();
+        if constexpr (Vel<i>::x != 0) { SA[0] += (w * Vel<i>::x) * v.x; SB[0] += (w * Vel<i>::x) * v.y; }
+        if constexpr (Vel<i>::y != 0) { SA[1] += (w * Vel<i>::y) * v.x; SB[1] += (w * Vel<i>::y) * v.y; }
+        if constexpr (Vel<i>::z != 0) { SA[2] += (w * Vel<i>::z) * v.x; SB[2] += (w * Vel<i>::z) * v.y; }
+    });
+}
+
+}  // namespace lbgb

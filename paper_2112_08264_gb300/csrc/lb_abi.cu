@@ -1,0 +1,362 @@
+// lb_abi.cu -- the C ABI declared in include/lb.h.
+//
+// The library allocates no device memory: lb_create carves the caller's
+// workspace into the two population buffers of the one-step two-grid scheme
+// (Sec. 3), the solid mask and flags, density scratch, reduction scratch and,
+// when recording for the adjoint, the checkpoints and adjoint buffers.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include <cuda_runtime.h>
+
+#include "adjoint.h"
+#include "kernels.h"
+#include "lb.h"
+
+using namespace lbgb;
+
+namespace {
+
+thread_local char g_last_error[256] = "";
+
+void set_error(const char* what, cudaError_t e) {
+    std::snprintf(g_last_error, sizeof g_last_error, "%s: %s", what, cudaGetErrorString(e));
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+size_t store_bytes(int prec) { return prec == LB_FP32 ? 4 : 2; }
+
+struct Layout {
+    size_t pop[2], mask, flags, rho, red_part, red_out;
+    size_t ckpt, ckpt_slots, seg, adj;
+    size_t state_bytes;
+    size_t total;
+};
+
+bool valid_dims(int nx, int ny, int nz) {
+    if (nx < 3 || ny < 3 || nz < 3) return false;
+    const long long N = (long long)nx * ny * nz;
+    return N < (1LL << 31);
+}
+
+bool valid_options(const lb_options& o) {
+    if (o.prec < LB_FP32 || o.prec > LB_BF16_DEV) return false;
+    if (o.kernel < LB_KERNEL_FUSED || o.kernel > LB_KERNEL_TWO_PASS) return false;
+    if (!std::isfinite(o.rho0_A) || !std::isfinite(o.rho0_B)) return false;
+    for (double g : o.body_force)
+        if (!std::isfinite(g)) return false;
+    if (o.ckpt_every < 0 || o.ckpt_steps_max < 0) return false;
+    if (o.ckpt_every > 0 && o.ckpt_steps_max < 1) return false;
+    return true;
+}
+
+Layout make_layout(int nx, int ny, int nz, const lb_options& o) {
+    Layout L{};
+    const size_t N = (size_t)nx * ny * nz;
+    L.state_bytes = align256(2 * Q * N * store_bytes(o.prec));
+    size_t off = 0;
+    L.pop[0] = off; off += L.state_bytes;
+    L.pop[1] = off; off += L.state_bytes;
+    L.mask = off; off += align256(N);
+    L.flags = off; off += align256(N * 4);
+    L.rho = off; off += align256(2 * N * 4);
+    L.red_part = off; off += align256((size_t)kRedBlocks * kRedVals * 8);
+    L.red_out = off; off += align256(kRedVals * 8);
+    if (o.ckpt_every > 0) {
+        L.ckpt_slots = (size_t)(o.ckpt_steps_max / o.ckpt_every) + 1;
+        L.ckpt = off; off += L.ckpt_slots * L.state_bytes;
+        L.seg = off; off += (size_t)o.ckpt_every * L.state_bytes;   // states of one segment
+        L.adj = off; off += adjoint_workspace_bytes(nx, ny, nz, o.ckpt_every);
+    }
+    L.total = off;
+    return L;
+}
+
+}  // namespace
+
+struct lb_ctx {
+    Geom g;
+    Phys p;
+    lb_options opt;
+    float tau, G;
+    cudaStream_t stream;
+    char* ws;
+    Layout L;
+    void* pop[2];
+    int cur;
+    bool has_mask;
+    uint8_t* mask_dev;
+    uint32_t* flags;
+    float* rho;
+    double* red_part;
+    double* red_out;
+    bool initialized;
+    long long steps;
+    int sm_count, tiles, zsplit, threads;
+    // recording for the adjoint
+    bool recording;       // lb_init was called with ckpt_every > 0 and the run is intact
+    double rho0_d[2];
+};
+
+namespace {
+
+Phys make_phys(float tau, float G, const lb_options& o) {
+    Phys p{};
+    p.tau = tau;
+    p.omega = 1.0f / tau;
+    p.G = G;
+    for (int a = 0; a < 3; ++a) p.g[a] = (float)o.body_force[a];
+    p.rho0[0] = p.rho0[1] = 1.0f;
+    return p;
+}
+
+lb_status cuda_status(const char* what, cudaError_t e) {
+    if (e == cudaSuccess) return LB_OK;
+    set_error(what, e);
+    return LB_ECUDA;
+}
+
+lb_status run_reduction(lb_ctx* c, double out[kRedVals], bool stats, const float* rA = nullptr,
+                        const float* rB = nullptr, const float* u = nullptr) {
+    cudaError_t e = stats ? launch_stats(c->opt.prec, c->pop[c->cur], c->has_mask ? c->flags : nullptr,
+                                         c->red_part, c->red_out, c->g, c->p, c->stream)
+                          : launch_check_init(rA, rB, u, c->has_mask ? c->flags : nullptr, c->red_part,
+                                              c->red_out, c->g, c->stream);
+    if (e != cudaSuccess) return cuda_status("reduction launch", e);
+    e = cudaMemcpyAsync(out, c->red_out, kRedVals * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_status("reduction copy", e);
+    return cuda_status("reduction sync", cudaStreamSynchronize(c->stream));
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+void lb_default_options(lb_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->prec = LB_FP32;
+    o->kernel = LB_KERNEL_FUSED;
+}
+
+size_t lb_workspace_bytes(int nx, int ny, int nz, const lb_options* opt) {
+    lb_options o;
+    lb_default_options(&o);
+    if (opt) o = *opt;
+    if (!valid_dims(nx, ny, nz) || !valid_options(o)) return 0;
+    return make_layout(nx, ny, nz, o).total;
+}
+
+lb_status lb_create(int nx, int ny, int nz, float tau, float G, const uint8_t* mask, const lb_options* opt,
+                    void* d_workspace, size_t ws_bytes, void* stream, lb_ctx** out) {
+    if (!out) return LB_EINVAL;
+    *out = nullptr;
+    lb_options o;
+    lb_default_options(&o);
+    if (opt) o = *opt;
+    if (!valid_dims(nx, ny, nz) || !valid_options(o)) return LB_EINVAL;
+    if (!std::isfinite(tau) || !(tau > 0.5f) || !std::isfinite(G)) return LB_EINVAL;
+    if (!d_workspace || ((uintptr_t)d_workspace & 255u)) return LB_EINVAL;
+    const Layout L = make_layout(nx, ny, nz, o);
+    if (ws_bytes < L.total) return LB_ENOMEM;
+
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_status("device query", e);
+
+    lb_ctx* c = new (std::nothrow) lb_ctx();
+    if (!c) return LB_EINVAL;
+    c->g.nx = nx; c->g.ny = ny; c->g.nz = nz;
+    c->g.plane = nx * ny;
+    c->g.N = (long long)nx * ny * nz;
+    c->opt = o;
+    c->tau = tau;
+    c->G = G;
+    c->p = make_phys(tau, G, o);
+    c->stream = static_cast<cudaStream_t>(stream);
+    c->ws = static_cast<char*>(d_workspace);
+    c->L = L;
+    c->pop[0] = c->ws + L.pop[0];
+    c->pop[1] = c->ws + L.pop[1];
+    c->cur = 0;
+    c->mask_dev = reinterpret_cast<uint8_t*>(c->ws + L.mask);
+    c->flags = reinterpret_cast<uint32_t*>(c->ws + L.flags);
+    c->rho = reinterpret_cast<float*>(c->ws + L.rho);
+    c->red_part = reinterpret_cast<double*>(c->ws + L.red_part);
+    c->red_out = reinterpret_cast<double*>(c->ws + L.red_out);
+    c->has_mask = mask != nullptr;
+    c->sm_count = sms;
+    fused_geometry(nx, ny, nz, sms, &c->tiles, &c->zsplit, &c->threads);
+
+    if (mask) {
+        e = cudaMemcpyAsync(c->mask_dev, mask, (size_t)c->g.N, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = launch_flags(c->mask_dev, c->flags, c->g, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            delete c;
+            return cuda_status("mask upload", e);
+        }
+    }
+    *out = c;
+    return LB_OK;
+}
+
+lb_status lb_set_stream(lb_ctx* c, void* stream) {
+    if (!c) return LB_EINVAL;
+    c->stream = static_cast<cudaStream_t>(stream);
+    return LB_OK;
+}
+
+lb_status lb_init(lb_ctx* c, const float* rA, const float* rB, const float* u) {
+    if (!c || !rA || !rB) return LB_EINVAL;
+    double red[kRedVals];
+    lb_status s = run_reduction(c, red, false, rA, rB, u);
+    if (s != LB_OK) return s;
+    if (red[3] > 0.0) return LB_EINVAL;
+    const double n = red[2] > 0.0 ? red[2] : 1.0;
+    c->rho0_d[0] = c->opt.rho0_A > 0.0 ? c->opt.rho0_A : (red[2] > 0.0 ? red[0] / n : 1.0);
+    c->rho0_d[1] = c->opt.rho0_B > 0.0 ? c->opt.rho0_B : (red[2] > 0.0 ? red[1] / n : 1.0);
+    c->p.rho0[0] = (float)c->rho0_d[0];
+    c->p.rho0[1] = (float)c->rho0_d[1];
+    c->cur = 0;
+    cudaError_t e = launch_unstream(c->opt.prec, c->pop[0], c->has_mask ? c->flags : nullptr, nullptr, rA, rB,
+                                    u, c->g, c->p, c->stream);
+    if (e == cudaSuccess && c->opt.ckpt_every > 0)
+        e = cudaMemcpyAsync(c->ws + c->L.ckpt, c->pop[0], c->L.state_bytes, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_status("init", e);
+    c->initialized = true;
+    c->steps = 0;
+    c->recording = c->opt.ckpt_every > 0 && u == nullptr;
+    return LB_OK;
+}
+
+lb_status lb_step(lb_ctx* c, int n) {
+    if (!c || n < 1) return LB_EINVAL;
+    if (!c->initialized) return LB_ESTATE;
+    const int K = c->opt.ckpt_every;
+    if (K > 0 && c->recording && c->steps + n > c->opt.ckpt_steps_max) return LB_ESTATE;
+    StepLaunch S;
+    S.prec = c->opt.prec;
+    S.kernel = c->opt.kernel;
+    S.flags = c->has_mask ? c->flags : nullptr;
+    S.rho = c->rho;
+    S.rho_out = nullptr;
+    S.g = c->g;
+    S.p = c->p;
+    S.zsplit = c->zsplit;
+    for (int t = 0; t < n; ++t) {
+        S.src = c->pop[c->cur];
+        S.dst = c->pop[1 - c->cur];
+        cudaError_t e = launch_step(S, c->stream);
+        if (e != cudaSuccess) return cuda_status("step", e);
+        c->cur ^= 1;
+        c->steps += 1;
+        if (K > 0 && c->recording && c->steps % K == 0) {
+            const size_t slot = (size_t)(c->steps / K);
+            e = cudaMemcpyAsync(c->ws + c->L.ckpt + slot * c->L.state_bytes, c->pop[c->cur], c->L.state_bytes,
+                                cudaMemcpyDeviceToDevice, c->stream);
+            if (e != cudaSuccess) return cuda_status("checkpoint", e);
+        }
+    }
+    return LB_OK;
+}
+
+lb_status lb_moments(lb_ctx* c, float* rA, float* rB, float* u) {
+    if (!c) return LB_EINVAL;
+    if (!c->initialized) return LB_ESTATE;
+    const uint32_t* fl = c->has_mask ? c->flags : nullptr;
+    cudaError_t e = cudaSuccess;
+    if (u) e = launch_densities(c->opt.prec, c->pop[c->cur], fl, c->rho, c->g, c->p, c->stream);
+    if (e == cudaSuccess)
+        e = launch_moments(c->opt.prec, c->pop[c->cur], fl, c->rho, rA, rB, u, c->g, c->p, c->stream);
+    return cuda_status("moments", e);
+}
+
+lb_status lb_stats(lb_ctx* c, double out5[5]) {
+    if (!c || !out5) return LB_EINVAL;
+    if (!c->initialized) return LB_ESTATE;
+    double red[kRedVals];
+    lb_status s = run_reduction(c, red, true);
+    if (s != LB_OK) return s;
+    for (int q = 0; q < 5; ++q) out5[q] = red[q];
+    return red[5] > 0.0 ? LB_ENONFINITE : LB_OK;
+}
+
+lb_status lb_get_state(lb_ctx* c, float* dst) {
+    if (!c || !dst) return LB_EINVAL;
+    if (!c->initialized) return LB_ESTATE;
+    return cuda_status("get_state", launch_get_state(c->opt.prec, c->pop[c->cur], c->has_mask ? c->flags : nullptr,
+                                                     dst, c->g, c->p, c->stream));
+}
+
+lb_status lb_set_state(lb_ctx* c, const float* src) {
+    if (!c || !src) return LB_EINVAL;
+    if (!c->initialized) return LB_ESTATE;
+    c->recording = false;   // the recorded trajectory no longer leads to this state
+    return cuda_status("set_state", launch_unstream(c->opt.prec, c->pop[c->cur], c->has_mask ? c->flags : nullptr,
+                                                    src, nullptr, nullptr, nullptr, c->g, c->p, c->stream));
+}
+
+long long lb_steps_done(const lb_ctx* c) { return c ? c->steps : -1; }
+
+lb_status lb_backward(lb_ctx* c, const float* dLA, const float* dLB, float* gA, float* gB, double* gG) {
+    if (!c) return LB_EINVAL;
+    if (!c->initialized || !c->recording || c->opt.ckpt_every <= 0 || c->steps < 1) return LB_ESTATE;
+    AdjointRun R;
+    R.prec = c->opt.prec;
+    R.flags = c->has_mask ? c->flags : nullptr;
+    R.g = c->g;
+    R.p = c->p;
+    R.K = c->opt.ckpt_every;
+    R.steps = c->steps;
+    R.state_bytes = c->L.state_bytes;
+    R.ckpt = c->ws + c->L.ckpt;
+    R.seg = c->ws + c->L.seg;
+    R.adj = c->ws + c->L.adj;
+    R.scratch = c->pop[1 - c->cur];
+    R.rho = c->rho;
+    R.red_part = c->red_part;
+    R.red_out = c->red_out;
+    R.zsplit = c->zsplit;
+    R.kernel = c->opt.kernel;
+    double gG_host = 0.0;
+    cudaError_t e = run_adjoint(R, dLA, dLB, gA, gB, &gG_host, c->stream);
+    if (e != cudaSuccess) return cuda_status("backward", e);
+    if (gG) *gG = gG_host;
+    return LB_OK;
+}
+
+lb_status lb_launch_info(const lb_ctx* c, int* launches, int* blocks, int* threads, int* zsplit) {
+    if (!c) return LB_EINVAL;
+    if (launches) *launches = c->opt.kernel == LB_KERNEL_FUSED ? 1 : 2;
+    if (blocks) *blocks = c->opt.kernel == LB_KERNEL_FUSED ? c->tiles * c->zsplit : (int)((c->g.N + 255) / 256);
+    if (threads) *threads = c->opt.kernel == LB_KERNEL_FUSED ? c->threads : 256;
+    if (zsplit) *zsplit = c->zsplit;
+    return LB_OK;
+}
+
+void lb_destroy(lb_ctx* c) { delete c; }
+
+const char* lb_status_str(lb_status s) {
+    switch (s) {
+        case LB_OK: return "ok";
+        case LB_EINVAL: return "invalid argument";
+        case LB_ENOMEM: return "workspace too small";
+        case LB_ECUDA: return "CUDA error";
+        case LB_ENONFINITE: return "non-finite population";
+        case LB_ESTATE: return "invalid state for this call";
+        case LB_ETIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+const char* lb_last_error(void) { return g_last_error; }
+
+}  // extern "C"

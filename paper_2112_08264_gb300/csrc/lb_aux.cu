@@ -1,0 +1,320 @@
+// lb_aux.cu -- kernels around the time step: solid flags, initial state
+// (equilibrium, Eq. LEQ) and state import/export, moments, and the FP64
+// conservation reduction.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "reduce.cuh"
+
+namespace lbgb {
+
+namespace {
+
+__device__ __forceinline__ void site_xyz(long long s, const Geom& g, int& x, int& y, int& z) {
+    x = (int)(s % g.nx);
+    y = (int)((s / g.nx) % g.ny);
+    z = (int)(s / g.plane);
+}
+
+__global__ void flags_kernel(const uint8_t* __restrict__ mask, uint32_t* __restrict__ flags, Geom g) {
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.N) return;
+    int x, y, z;
+    site_xyz(s, g, x, y, z);
+    PullIdx P;
+    pull_indices(g, x, y, z, P);
+    uint32_t f = mask[s] ? kSolid : 0u;
+    static_for<1, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        if (mask[P.src[i]]) f |= (1u << i);
+    });
+    flags[s] = f;
+}
+
+// g_j(y) = f_j(y + c_j) if y + c_j is fluid, else f_opp(j)(y); f is either the
+// given field or the equilibrium of (rho^k, u).
+template <typename S, bool FROM_F>
+__global__ void unstream_kernel(S* __restrict__ dst, const uint32_t* __restrict__ flags,
+                                const float* __restrict__ f, const float* __restrict__ rhoA,
+                                const float* __restrict__ rhoB, const float* __restrict__ u, Geom g,
+                                Phys p) {
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.N) return;
+    int x, y, z;
+    site_xyz(s, g, x, y, z);
+    const uint32_t fl = flags ? flags[s] : 0u;
+    if (fl & kSolid) {
+        for (int j = 0; j < 2 * Q; ++j) Store<S>::st(dst + (size_t)j * g.N + s, 0.f);
+        return;
+    }
+    const int xm = wrap_dec(x, g.nx), xp = wrap_inc(x, g.nx);
+    const int ym = wrap_dec(y, g.ny), yp = wrap_inc(y, g.ny);
+    const int zm = wrap_dec(z, g.nz), zp = wrap_inc(z, g.nz);
+    static_for<0, Q>([&](auto J) {
+        constexpr int j = decltype(J)::value;
+        // destination neighbour y + c_j is solid <=> flag bit opp(j) (y - c_opp(j))
+        const bool back = (j != 0) && (fl & (1u << Vel<j>::opp));
+        const int tx = Vel<j>::x == 1 ? xp : (Vel<j>::x == -1 ? xm : x);
+        const int ty = Vel<j>::y == 1 ? yp : (Vel<j>::y == -1 ? ym : y);
+        const int tz = Vel<j>::z == 1 ? zp : (Vel<j>::z == -1 ? zm : z);
+        const long long t = back ? s : (tx + (long long)g.nx * (ty + (long long)g.ny * tz));
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            float dev;
+            if constexpr (FROM_F) {
+                const int pop = back ? Vel<j>::opp : j;
+                dev = f[(size_t)(k * Q + pop) * g.N + t] - wgt<j>() * p.rho0[k];
+            } else {
+                const float r = (k == 0 ? rhoA : rhoB)[t];
+                float uu = 0.f, cu = 0.f;
+                if (u) {
+                    const float u0 = u[t], u1 = u[g.N + t], u2 = u[2 * g.N + t];
+                    uu = u0 * u0 + u1 * u1 + u2 * u2;
+                    cu = Vel<j>::x * u0 + Vel<j>::y * u1 + Vel<j>::z * u2;
+                    if (back) cu = -cu;   // velocity opp(j) at node y
+                }
+                dev = wgt<j>() * ((r - p.rho0[k]) + r * (cu * (3.0f + 4.5f * cu) - 1.5f * uu));
+            }
+            Store<S>::st(dst + (size_t)(k * Q + j) * g.N + s, dev);
+        }
+    });
+}
+
+template <typename S, bool MASK>
+__global__ void get_state_kernel(const S* __restrict__ src, const uint32_t* __restrict__ flags,
+                                 float* __restrict__ f, Geom g, Phys p) {
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.N) return;
+    int x, y, z;
+    site_xyz(s, g, x, y, z);
+    uint32_t fl = 0;
+    if constexpr (MASK) {
+        fl = flags[s];
+        if (fl & kSolid) {
+            for (int j = 0; j < 2 * Q; ++j) f[(size_t)j * g.N + s] = 0.f;
+            return;
+        }
+    }
+    PullIdx P;
+    pull_indices(g, x, y, z, P);
+    float d[2][Q];
+    pull<S, MASK>(src, g, P, fl, d);
+    static_for<0, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) f[(size_t)(k * Q + i) * g.N + s] = wgt<i>() * p.rho0[k] + d[k][i];
+    });
+}
+
+template <typename S, bool MASK>
+__global__ void densities_kernel(const S* __restrict__ src, const uint32_t* __restrict__ flags,
+                                 float* __restrict__ rho, Geom g, Phys p) {
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.N) return;
+    int x, y, z;
+    site_xyz(s, g, x, y, z);
+    const float2 r = density_at<S, MASK>(src, flags, g, p, x, y, z);
+    rho[s] = r.x;
+    rho[g.N + s] = r.y;
+}
+
+// rho^k, and u = (j + (F^A + F^B) / 2) / rho with F^A = -G psi^A S^B + rho^A g.
+template <typename S, bool MASK>
+__global__ void moments_kernel(const S* __restrict__ src, const uint32_t* __restrict__ flags,
+                               const float* __restrict__ rho, float* __restrict__ oA, float* __restrict__ oB,
+                               float* __restrict__ ou, Geom g, Phys p) {
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.N) return;
+    int x, y, z;
+    site_xyz(s, g, x, y, z);
+    uint32_t fl = 0;
+    if constexpr (MASK) fl = flags[s];
+    if (fl & kSolid) {
+        if (oA) oA[s] = 0.f;
+        if (oB) oB[s] = 0.f;
+        if (ou) ou[s] = ou[g.N + s] = ou[2 * g.N + s] = 0.f;
+        return;
+    }
+    PullIdx P;
+    pull_indices(g, x, y, z, P);
+    float d[2][Q];
+    pull<S, MASK>(src, g, P, fl, d);
+    float dA, dB, j[3];
+    sums(d, dA, dB, j);
+    const float rA = p.rho0[0] + dA, rB = p.rho0[1] + dB;
+    if (oA) oA[s] = rA;
+    if (oB) oB[s] = rB;
+    if (!ou) return;
+    float SA[3], SB[3];
+    neighbour_sums(
+        [&](int dx, int dy, int dz) {
+            const int xx = dx > 0 ? wrap_inc(x, g.nx) : (dx < 0 ? wrap_dec(x, g.nx) : x);
+            const int yy = dy > 0 ? wrap_inc(y, g.ny) : (dy < 0 ? wrap_dec(y, g.ny) : y);
+            const int zz = dz > 0 ? wrap_inc(z, g.nz) : (dz < 0 ? wrap_dec(z, g.nz) : z);
+            const long long t = xx + (long long)g.nx * (yy + (long long)g.ny * zz);
+            return make_float2(rho[t], rho[g.N + t]);
+        },
+        SA, SB);
+    const float inv = 1.0f / (rA + rB);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float F = -p.G * (rA * SB[a] + rB * SA[a]) + (rA + rB) * p.g[a];
+        ou[a * g.N + s] = (j[a] + 0.5f * F) * inv;
+    }
+}
+
+// ---- FP64 reductions ----
+
+template <typename S, bool MASK>
+__global__ void __launch_bounds__(256)
+stats_kernel(const S* __restrict__ src, const uint32_t* __restrict__ flags, double* __restrict__ partials,
+             Geom g, Phys p) {
+    double v[kRedVals] = {0, 0, 0, 0, 0, 0};
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.N; s += stride) {
+        int x, y, z;
+        site_xyz(s, g, x, y, z);
+        uint32_t fl = 0;
+        if constexpr (MASK) {
+            fl = flags[s];
+            if (fl & kSolid) continue;
+        }
+        PullIdx P;
+        pull_indices(g, x, y, z, P);
+        float d[2][Q];
+        pull<S, MASK>(src, g, P, fl, d);
+        // per-node sums in FP32 (19 terms), accumulated across nodes in FP64
+        float dA, dB, j[3];
+        sums(d, dA, dB, j);
+        v[0] += (double)p.rho0[0] + (double)dA;
+        v[1] += (double)p.rho0[1] + (double)dB;
+        v[2] += (double)j[0];
+        v[3] += (double)j[1];
+        v[4] += (double)j[2];
+        v[5] += (isfinite(dA) && isfinite(dB) && isfinite(j[0]) && isfinite(j[1]) && isfinite(j[2])) ? 0.0 : 1.0;
+    }
+    block_sum_store(v, partials + (size_t)blockIdx.x * kRedVals);
+}
+
+__global__ void check_init_kernel(const float* __restrict__ rA, const float* __restrict__ rB,
+                                  const float* __restrict__ u, const uint32_t* __restrict__ flags,
+                                  double* __restrict__ partials, Geom g) {
+    double v[kRedVals] = {0, 0, 0, 0, 0, 0};
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.N; s += stride) {
+        if (flags && (flags[s] & kSolid)) continue;
+        const float a = rA[s], b = rB[s];
+        bool ok = (a > 0.f) && (b > 0.f) && isfinite(a) && isfinite(b);
+        if (u) ok = ok && isfinite(u[s]) && isfinite(u[g.N + s]) && isfinite(u[2 * g.N + s]);
+        v[0] += a;
+        v[1] += b;
+        v[2] += 1.0;
+        v[3] += ok ? 0.0 : 1.0;
+    }
+    block_sum_store(v, partials + (size_t)blockIdx.x * kRedVals);
+}
+
+// Sum nblk rows of partials in a fixed order (one block).
+__global__ void __launch_bounds__(256) finish_kernel(const double* __restrict__ partials, int nblk,
+                                                     double* __restrict__ out) {
+    double v[kRedVals] = {0, 0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x)
+#pragma unroll
+        for (int q = 0; q < kRedVals; ++q) v[q] += partials[(size_t)b * kRedVals + q];
+    block_sum_store(v, out);
+}
+
+unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+template <typename F4, typename F3, typename F2>
+cudaError_t by_prec(int prec, F4&& f32, F3&& f16, F2&& bf16) {
+    switch (prec) {
+        case 0: f32(); break;
+        case 1: f16(); break;
+        case 2: bf16(); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_flags(const uint8_t* mask, uint32_t* flags, const Geom& g, cudaStream_t st) {
+    flags_kernel<<<blocks_for(g.N, 256), 256, 0, st>>>(mask, flags, g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unstream(int prec, void* dst, const uint32_t* flags, const float* f, const float* rhoA,
+                            const float* rhoB, const float* u, const Geom& g, const Phys& p,
+                            cudaStream_t st) {
+    const unsigned nb = blocks_for(g.N, 256);
+#define LBGB_UNSTREAM(T)                                                                          \
+    [&] {                                                                                         \
+        if (f) unstream_kernel<T, true><<<nb, 256, 0, st>>>((T*)dst, flags, f, rhoA, rhoB, u, g, p); \
+        else unstream_kernel<T, false><<<nb, 256, 0, st>>>((T*)dst, flags, f, rhoA, rhoB, u, g, p); \
+    }
+    return by_prec(prec, LBGB_UNSTREAM(float), LBGB_UNSTREAM(__half), LBGB_UNSTREAM(__nv_bfloat16));
+#undef LBGB_UNSTREAM
+}
+
+cudaError_t launch_get_state(int prec, const void* src, const uint32_t* flags, float* f, const Geom& g,
+                             const Phys& p, cudaStream_t st) {
+    const unsigned nb = blocks_for(g.N, 256);
+#define LBGB_GET(T)                                                                          \
+    [&] {                                                                                    \
+        if (flags) get_state_kernel<T, true><<<nb, 256, 0, st>>>((const T*)src, flags, f, g, p); \
+        else get_state_kernel<T, false><<<nb, 256, 0, st>>>((const T*)src, flags, f, g, p);      \
+    }
+    return by_prec(prec, LBGB_GET(float), LBGB_GET(__half), LBGB_GET(__nv_bfloat16));
+#undef LBGB_GET
+}
+
+cudaError_t launch_densities(int prec, const void* src, const uint32_t* flags, float* rho, const Geom& g,
+                             const Phys& p, cudaStream_t st) {
+    const unsigned nb = blocks_for(g.N, 256);
+#define LBGB_DEN(T)                                                                           \
+    [&] {                                                                                     \
+        if (flags) densities_kernel<T, true><<<nb, 256, 0, st>>>((const T*)src, flags, rho, g, p); \
+        else densities_kernel<T, false><<<nb, 256, 0, st>>>((const T*)src, flags, rho, g, p);      \
+    }
+    return by_prec(prec, LBGB_DEN(float), LBGB_DEN(__half), LBGB_DEN(__nv_bfloat16));
+#undef LBGB_DEN
+}
+
+cudaError_t launch_moments(int prec, const void* src, const uint32_t* flags, const float* rho, float* rhoA,
+                           float* rhoB, float* u, const Geom& g, const Phys& p, cudaStream_t st) {
+    const unsigned nb = blocks_for(g.N, 256);
+#define LBGB_MOM(T)                                                                                  \
+    [&] {                                                                                            \
+        if (flags) moments_kernel<T, true><<<nb, 256, 0, st>>>((const T*)src, flags, rho, rhoA, rhoB, u, g, p); \
+        else moments_kernel<T, false><<<nb, 256, 0, st>>>((const T*)src, flags, rho, rhoA, rhoB, u, g, p);      \
+    }
+    return by_prec(prec, LBGB_MOM(float), LBGB_MOM(__half), LBGB_MOM(__nv_bfloat16));
+#undef LBGB_MOM
+}
+
+cudaError_t launch_stats(int prec, const void* src, const uint32_t* flags, double* partials, double* out,
+                         const Geom& g, const Phys& p, cudaStream_t st) {
+#define LBGB_STATS(T)                                                                              \
+    [&] {                                                                                          \
+        if (flags) stats_kernel<T, true><<<kRedBlocks, 256, 0, st>>>((const T*)src, flags, partials, g, p); \
+        else stats_kernel<T, false><<<kRedBlocks, 256, 0, st>>>((const T*)src, flags, partials, g, p);      \
+    }
+    cudaError_t e = by_prec(prec, LBGB_STATS(float), LBGB_STATS(__half), LBGB_STATS(__nv_bfloat16));
+#undef LBGB_STATS
+    if (e != cudaSuccess) return e;
+    finish_kernel<<<1, 256, 0, st>>>(partials, kRedBlocks, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_init(const float* rhoA, const float* rhoB, const float* u, const uint32_t* flags,
+                              double* partials, double* out, const Geom& g, cudaStream_t st) {
+    check_init_kernel<<<kRedBlocks, 256, 0, st>>>(rhoA, rhoB, u, flags, partials, g);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    finish_kernel<<<1, 256, 0, st>>>(partials, kRedBlocks, out);
+    return cudaGetLastError();
+}
+
+}  // namespace lbgb

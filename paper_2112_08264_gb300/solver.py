@@ -1,0 +1,174 @@
+"""Python face of the C ABI: a solver object over a torch-allocated workspace.
+
+PyTorch only provides device memory and the stream; every step of the method
+runs in the library's CUDA kernels (``include/lb.h``). Field tensors are
+float32, contiguous, on the solver's device, shaped ``(nz, ny, nx)`` (or any
+shape with N elements); velocities ``(3, nz, ny, nx)``; populations
+``(2, 19, nz, ny, nx)`` in the public velocity order of ``include/lb.h``.
+"""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+
+
+def _ptr(t, n, what, optional=False):
+    if t is None:
+        if optional:
+            return None
+        raise ValueError("%s is required" % what)
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % what)
+    if t.dtype != torch.float32 or not t.is_contiguous() or t.numel() != n:
+        raise ValueError("%s must be a contiguous float32 tensor with %d elements" % (what, n))
+    return t.data_ptr()
+
+
+class Solver:
+    """Two-component D3Q19 BGK Shan-Chen lattice-Boltzmann solver on one GPU.
+
+    Parameters follow ``lb_create``: grid ``nx, ny, nz``, relaxation time
+    ``tau`` (> 1/2), coupling ``G``, optional solid ``mask`` (numpy uint8,
+    shape (nz, ny, nx), 1 = solid), storage ``prec`` in {"fp32", "fp16",
+    "bf16"}, ``kernel`` in {"fused", "two_pass"}, deviation base ``rho0``
+    (0 = mean of the initial densities), ``body_force`` g, and checkpoint
+    recording for ``backward`` (``ckpt_every`` K, ``ckpt_steps_max``).
+    """
+
+    def __init__(self, nx, ny, nz, tau, G, mask=None, prec="fp32", kernel="fused", rho0=(0.0, 0.0),
+                 body_force=(0.0, 0.0, 0.0), ckpt_every=0, ckpt_steps_max=0, device=None, stream=None):
+        L = _lib.lib()
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.shape = (self.nz, self.ny, self.nx)
+        self.N = self.nx * self.ny * self.nz
+        self.tau, self.G = float(tau), float(G)
+        self.prec, self.kernel = prec, kernel
+        self.opt = _lib.options(prec, kernel, rho0, body_force, ckpt_every, ckpt_steps_max)
+        nbytes = _lib.workspace_bytes(self.nx, self.ny, self.nz, self.opt)
+        if nbytes == 0:
+            raise ValueError("invalid grid or options")
+        self.device = torch.device(device if device is not None else "cuda")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.mask = None
+        mptr = None
+        if mask is not None:
+            self.mask = np.ascontiguousarray(mask, dtype=np.uint8)
+            if self.mask.size != self.N:
+                raise ValueError("mask must have nx*ny*nz elements")
+            mptr = self.mask.ctypes.data_as(ctypes.c_void_p)
+        h = ctypes.c_void_p()
+        _lib.check(L.lb_create(self.nx, self.ny, self.nz, self.tau, self.G, mptr, ctypes.byref(self.opt),
+                               self.workspace.data_ptr(), nbytes, self.stream.cuda_stream, ctypes.byref(h)),
+                   "lb_create")
+        self._h = h
+
+    # -- lifecycle ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.lib().lb_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_stream(self, stream):
+        self.stream = stream
+        _lib.check(_lib.lib().lb_set_stream(self._h, stream.cuda_stream), "lb_set_stream")
+
+    # -- the method ----------------------------------------------------------
+    def init(self, rhoA, rhoB, u=None):
+        """Equilibrium initial state from device fields rho^A, rho^B (and u)."""
+        _lib.check(_lib.lib().lb_init(self._h, _ptr(rhoA, self.N, "rhoA"), _ptr(rhoB, self.N, "rhoB"),
+                                      _ptr(u, 3 * self.N, "u", optional=True)), "lb_init")
+
+    def step(self, n=1):
+        _lib.check(_lib.lib().lb_step(self._h, int(n)), "lb_step")
+
+    def moments(self, velocity=True):
+        """(rho_A, rho_B, u or None) as new device tensors."""
+        rA = torch.empty(self.shape, dtype=torch.float32, device=self.device)
+        rB = torch.empty(self.shape, dtype=torch.float32, device=self.device)
+        u = torch.empty((3,) + self.shape, dtype=torch.float32, device=self.device) if velocity else None
+        _lib.check(_lib.lib().lb_moments(self._h, rA.data_ptr(), rB.data_ptr(),
+                                         u.data_ptr() if u is not None else None), "lb_moments")
+        return rA, rB, u
+
+    def stats(self):
+        """FP64 [mass_A, mass_B, Px, Py, Pz] (synchronous)."""
+        out = (ctypes.c_double * 5)()
+        _lib.check(_lib.lib().lb_stats(self._h, out), "lb_stats")
+        return np.array(out[:], dtype=np.float64)
+
+    def get_state(self, out=None):
+        if out is None:
+            out = torch.empty((2, 19) + self.shape, dtype=torch.float32, device=self.device)
+        _lib.check(_lib.lib().lb_get_state(self._h, _ptr(out, 38 * self.N, "out")), "lb_get_state")
+        return out
+
+    def set_state(self, f):
+        _lib.check(_lib.lib().lb_set_state(self._h, _ptr(f, 38 * self.N, "f")), "lb_set_state")
+
+    @property
+    def steps_done(self):
+        return int(_lib.lib().lb_steps_done(self._h))
+
+    def backward(self, dL_drhoA, dL_drhoB=None, want_rho=True):
+        """Gradients of a loss of the final densities of a recorded run:
+        (dL/drho_A0, dL/drho_B0, dL/dG)."""
+        gA = torch.empty(self.shape, dtype=torch.float32, device=self.device) if want_rho else None
+        gB = torch.empty(self.shape, dtype=torch.float32, device=self.device) if want_rho else None
+        gG = ctypes.c_double(0.0)
+        _lib.check(_lib.lib().lb_backward(
+            self._h, _ptr(dL_drhoA, self.N, "dL_drhoA", optional=True),
+            _ptr(dL_drhoB, self.N, "dL_drhoB", optional=True),
+            gA.data_ptr() if gA is not None else None, gB.data_ptr() if gB is not None else None,
+            ctypes.byref(gG)), "lb_backward")
+        return gA, gB, gG.value
+
+    def launch_info(self):
+        v = [ctypes.c_int() for _ in range(4)]
+        _lib.check(_lib.lib().lb_launch_info(self._h, *[ctypes.byref(x) for x in v]), "lb_launch_info")
+        return {"launches_per_step": v[0].value, "grid_blocks": v[1].value,
+                "block_threads": v[2].value, "z_split": v[3].value}
+
+
+def create(nx, ny, nz, tau, G, mask=None, **kw):
+    """``lb_create(nx, ny, nz, tau, G, mask)`` in Python form."""
+    return Solver(nx, ny, nz, tau, G, mask=mask, **kw)
+
+
+def run_host(rhoA, rhoB, steps, tau, G, mask=None, u=None, solver=None, **kw):
+    """End-to-end run from host arrays: copy the initial fields to the device
+    (from pinned memory), initialise, take ``steps`` steps, and copy rho_A,
+    rho_B and u back. Returns numpy arrays (rho_A, rho_B, u) and the solver."""
+    rhoA = np.ascontiguousarray(rhoA, dtype=np.float32)
+    nz, ny, nx = rhoA.shape
+    s = solver if solver is not None else Solver(nx, ny, nz, tau, G, mask=mask, **kw)
+    dev = s.device
+    hA = torch.from_numpy(rhoA).pin_memory()
+    hB = torch.from_numpy(np.ascontiguousarray(rhoB, dtype=np.float32)).pin_memory()
+    with torch.cuda.stream(s.stream):
+        dA = hA.to(dev, non_blocking=True)
+        dB = hB.to(dev, non_blocking=True)
+        du = None
+        if u is not None:
+            du = torch.from_numpy(np.ascontiguousarray(u, dtype=np.float32)).pin_memory().to(dev, non_blocking=True)
+    s.init(dA, dB, du)
+    s.step(steps)
+    rA, rB, uu = s.moments()
+    with torch.cuda.stream(s.stream):
+        out = [t.to("cpu", non_blocking=True) for t in (rA, rB, uu)]
+    s.stream.synchronize()
+    return tuple(t.numpy() for t in out), s

@@ -1,0 +1,100 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds and
+loads, exports every function ``include/lb.h`` declares, sizes workspaces and
+rejects invalid arguments before touching a device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2112_08264_gb300 import _lib, build
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "lb.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return _lib.lib()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"\b(lb_[a-z_0-9]+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("lb_create", "lb_init", "lb_step", "lb_moments", "lb_backward", "lb_stats",
+                 "lb_get_state", "lb_set_state", "lb_destroy", "lb_workspace_bytes", "lb_status_str"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(L):
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_library_is_sm103a_only():
+    # the build emits exactly one -gencode for sm_103a
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_workspace_bytes(L):
+    o = _lib.options()
+    n = 32 ** 3
+    wb = _lib.workspace_bytes(32, 32, 32, o)
+    assert wb >= 2 * 38 * n * 4 + 2 * n * 4 + n * 4 + n
+    o16 = _lib.options("fp16")
+    assert _lib.workspace_bytes(32, 32, 32, o16) < wb
+    oc = _lib.options(ckpt_every=10, ckpt_steps_max=50)
+    assert _lib.workspace_bytes(32, 32, 32, oc) > wb + 6 * 38 * n * 4
+    assert _lib.workspace_bytes(2, 32, 32, o) == 0          # dimension < 3
+    assert _lib.workspace_bytes(2048, 1024, 1024, o) == 0   # N >= 2^31
+    assert _lib.workspace_bytes(8, 8, 8, _lib.options(prec=7)) == 0
+    assert _lib.workspace_bytes(8, 8, 8, _lib.options(ckpt_every=4, ckpt_steps_max=0)) == 0
+
+
+@pytest.mark.parametrize("args", [
+    dict(nx=2, ny=8, nz=8, tau=1.0, G=0.5),
+    dict(nx=8, ny=8, nz=8, tau=0.5, G=0.5),
+    dict(nx=8, ny=8, nz=8, tau=float("nan"), G=0.5),
+    dict(nx=8, ny=8, nz=8, tau=1.0, G=float("inf")),
+])
+def test_create_rejects_bad_arguments(L, args):
+    o = _lib.options()
+    h = ctypes.c_void_p()
+    st = L.lb_create(args["nx"], args["ny"], args["nz"], args["tau"], args["G"], None, ctypes.byref(o),
+                     ctypes.c_void_p(1 << 20), 1 << 40, None, ctypes.byref(h))
+    assert st == _lib.LB_EINVAL
+    assert not h.value
+
+
+def test_create_rejects_short_or_misaligned_workspace(L):
+    o = _lib.options()
+    need = _lib.workspace_bytes(8, 8, 8, o)
+    h = ctypes.c_void_p()
+    assert L.lb_create(8, 8, 8, 1.0, 0.5, None, ctypes.byref(o), ctypes.c_void_p(1 << 20), need - 1, None,
+                       ctypes.byref(h)) == _lib.LB_ENOMEM
+    assert L.lb_create(8, 8, 8, 1.0, 0.5, None, ctypes.byref(o), ctypes.c_void_p((1 << 20) + 4), need, None,
+                       ctypes.byref(h)) == _lib.LB_EINVAL
+    assert L.lb_create(8, 8, 8, 1.0, 0.5, None, ctypes.byref(o), None, need, None,
+                       ctypes.byref(h)) == _lib.LB_EINVAL
+
+
+def test_null_context_calls_are_rejected(L):
+    assert L.lb_step(None, 1) == _lib.LB_EINVAL
+    assert L.lb_init(None, None, None, None) == _lib.LB_EINVAL
+    assert L.lb_moments(None, None, None, None) == _lib.LB_EINVAL
+    assert L.lb_stats(None, None) == _lib.LB_EINVAL
+    assert L.lb_backward(None, None, None, None, None, None) == _lib.LB_EINVAL
+    assert L.lb_steps_done(None) == -1
+    L.lb_destroy(None)
+
+
+def test_status_strings(L):
+    for s in range(7):
+        assert L.lb_status_str(s)
+    assert L.lb_status_str(99) == b"unknown status"
