@@ -161,11 +161,35 @@ lb_status lb_backward(lb_ctx* ctx, const float* d_dL_drhoA, const float* d_dL_dr
 lb_status lb_launch_info(const lb_ctx* ctx, int* launches_per_step, int* grid_blocks,
                          int* block_threads, int* z_split);
 
+/* Allocation-free moments of a caller's population field. The paper has no
+ * counterpart; this entry point exists for callers that may not allocate
+ * device memory at all (no cudaMalloc, no allocator of any library) and so
+ * cannot provide lb_create's workspace: for example code whose device memory
+ * belongs to another framework's pool, or a plugin that must not allocate
+ * after start-up. It computes, like lb_moments, rho^A, rho^B and the mixture
+ * velocity u = (sum_k sum_i c_i f_i^k + (F^A + F^B)/2) / (rho^A + rho^B)
+ * (0 at solid nodes), from
+ *   d_f     DEVICE post-streaming populations [k][i][s], 2*19*N floats (the
+ *           layout lb_get_state writes);
+ *   d_mask  DEVICE solid mask, N bytes, 1 = solid, or NULL (all fluid);
+ *   G, body_force (HOST, 3 doubles, or NULL = 0) as in lb_create/lb_options;
+ * into DEVICE outputs d_rhoA, d_rhoB (N floats) and d_u (3N floats SoA), any
+ * of which may be NULL. It allocates nothing and calls no allocator: the
+ * neighbour-density scratch it needs is a static device array of 2^20 nodes
+ * (8 MiB, held on every GPU that loads the library until the process exits).
+ * N = nx*ny*nz above 2^20 is rejected with LB_EINVAL and a message in
+ * lb_last_error(). The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress): make that first call before any stream
+ * capture. All calls share the array, so calls that overlap on the GPU race;
+ * serialise them. Asynchronous on `stream` (a cudaStream_t, NULL = legacy). */
+lb_status lb_moments_noalloc(int nx, int ny, int nz, float G, const double* body_force, const float* d_f,
+                             const uint8_t* d_mask, float* d_rhoA, float* d_rhoB, float* d_u, void* stream);
+
 /* Destroy the context (does not free the caller's workspace). NULL is a no-op. */
 void lb_destroy(lb_ctx* ctx);
 
 /* Static text for a status; text of the last CUDA error seen by the calling
- * thread ("" if none). */
+ * thread, or of the last rejection lb_moments_noalloc explained ("" if none). */
 const char* lb_status_str(lb_status s);
 const char* lb_last_error(void);
 

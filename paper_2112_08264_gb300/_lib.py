@@ -69,6 +69,9 @@ def lib():
     L.lb_steps_done.restype = ctypes.c_longlong
     L.lb_backward.argtypes = [_VP, _FP, _FP, _FP, _FP, ctypes.POINTER(ctypes.c_double)]
     L.lb_launch_info.argtypes = [_VP] + [ctypes.POINTER(ctypes.c_int)] * 4
+    L.lb_moments_noalloc.argtypes = ([ctypes.c_int] * 3 + [ctypes.c_float, ctypes.POINTER(ctypes.c_double),
+                                                             _FP, _VP, _FP, _FP, _FP, _VP])
+    L.lb_moments_noalloc.restype = ctypes.c_int
     L.lb_destroy.argtypes = [_VP]
     L.lb_destroy.restype = None
     L.lb_status_str.argtypes = [ctypes.c_int]

@@ -60,4 +60,7 @@ cudaError_t launch_stats(int prec, const void* src, const uint32_t* flags, doubl
 cudaError_t launch_check_init(const float* rhoA, const float* rhoB, const float* u, const uint32_t* flags,
                               double* partials, double* out, const Geom& g, cudaStream_t st);
 
+// Message returned by lb_last_error() (host code only).
+void record_error_text(const char* msg);
+
 }  // namespace lbgb

@@ -27,6 +27,15 @@ void set_error(const char* what, cudaError_t e) {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+}  // namespace
+
+namespace lbgb {
+// Message for lb_last_error() from code outside this file.
+void record_error_text(const char* msg) { std::snprintf(g_last_error, sizeof g_last_error, "%s", msg); }
+}  // namespace lbgb
+
+namespace {
+
 size_t store_bytes(int prec) { return prec == LB_FP32 ? 4 : 2; }
 
 struct Layout {
