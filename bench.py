@@ -136,9 +136,18 @@ def max_over_ranks(x, world):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    on_gpu = torch.cuda.is_available() and dist.get_backend() == "nccl"
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if on_gpu else "cpu")
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_throughput(ms_local, steps, sites_per_replica, world):
+    """Whole-job GLUPS of `world` independent replicas: all site updates over
+    the slowest rank's timed region (max over ranks), and that time per step."""
+    ms_max = max_over_ranks(ms_local, world)
+    step_s = ms_max / 1e3 / steps
+    return world * sites_per_replica / step_s / 1e9, step_s
 
 
 def workload(name, grid=None):
@@ -209,6 +218,36 @@ def time_e2e(W, prec, kernel, steps):
     h2d = 2 * n * 4
     d2h = 5 * n * 4
     return t1 - t0, h2d, d2h, bool(np.isfinite(oA).all())
+
+
+def time_adjoint(prec, kernel, n=128, steps=80, K=40, warmup=3):
+    """Differentiation form: forward with checkpoints every K steps, then
+    lb_backward; returns per-step ms of both and their ratio."""
+    import torch
+    from paper_2112_08264_gb300 import Solver, inputs
+    rA, rB = inputs.spinodal(n, n, n, seed=1234)
+    target = torch.tensor(inputs.smoothed_target(n, n, n, seed=99), dtype=torch.float32, device="cuda")
+    s = Solver(n, n, n, 1.0, 0.65, prec=prec, kernel=kernel, ckpt_every=K, ckpt_steps_max=steps)
+    dA = torch.tensor(rA, dtype=torch.float32, device="cuda")
+    dB = torch.tensor(rB, dtype=torch.float32, device="cuda")
+    fwd, bwd = [], []
+    for rep in range(warmup + 1):
+        s.init(dA, dB)
+        torch.cuda.synchronize()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(s.stream)
+        s.step(steps)
+        e1.record(s.stream)
+        fA, _, _ = s.moments(velocity=False)
+        s.backward((2.0 * (fA - target)).contiguous(), want_rho=True)
+        e2.record(s.stream)
+        e2.synchronize()
+        fwd.append(e0.elapsed_time(e1))
+        bwd.append(e1.elapsed_time(e2))
+    s.close()
+    f_ms, b_ms = fwd[-1] / steps, bwd[-1] / steps
+    return {"grid": [n, n, n], "steps": steps, "ckpt_every": K, "forward_ms_per_step": f_ms,
+            "backward_ms_per_step": b_ms, "backward_over_forward": b_ms / f_ms}
 
 
 def oracle_sample(shape, tau, G, budget_s, min_steps=1, max_steps=1000, per_step_budget=None):
@@ -327,9 +366,7 @@ def main():
         clocks = clk.summary()
         clocks["remeasured"] = True
     barrier(world)
-    ms_max = max_over_ranks(ms, world)
-    step_s = ms_max / 1e3 / args.steps
-    glups = world * N / step_s / 1e9
+    glups, step_s = replica_throughput(ms, args.steps, N, world)
 
     bps = BYTES_PER_SITE[args.prec]
     if W["mask"] is not None:
@@ -366,7 +403,7 @@ def main():
                        "what": "host arrays -> pinned H2D -> lb_init -> %d steps -> moments -> D2H" % args.steps}
     if rank == 0 and not args.no_variants:
         var = {}
-        for prec, kern in (("fp16", "fused"), ("bf16", "fused"), ("fp32", "two_pass")):
+        for prec, kern in (("fp16", "fused"), ("bf16", "fused"), ("fp32", "two_pass"), ("fp32", "fused_reg")):
             if (prec, kern) == (args.prec, args.kernel):
                 continue
             vms, vinfo, _ = time_device(W, prec, kern, args.steps, args.warmup)
@@ -378,6 +415,19 @@ def main():
         line["variants"] = var
         if "fp16_fused" in var and args.prec == "fp32":
             line["fp16_over_fp32"] = var["fp16_fused"]["GLUPS"] / glups
+        if args.config == "spinodal256" and args.grid is None:
+            W5 = workload("spinodal512")
+            N5 = 512 ** 3
+            c3 = {}
+            for prec in ("fp32", "fp16", "bf16"):
+                vms, _, _ = time_device(W5, prec, "fused", 100, 5)
+                vstep = vms / 1e3 / 100
+                c3[prec] = {"GLUPS": N5 / vstep / 1e9, "ms_per_step": vstep * 1e3,
+                            "hbm_frac_of_%s" % peak_kind: BYTES_PER_SITE[prec] * N5 / vstep / 1e9 / peak}
+            c3["fp16_over_fp32"] = c3["fp16"]["GLUPS"] / c3["fp32"]["GLUPS"]
+            line["precision_512"] = c3
+            del W5
+            line["adjoint_128"] = time_adjoint("fp32", "fused")
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = run_cpu_baseline(W)
     if rank == 0:

@@ -67,9 +67,12 @@ typedef enum { LB_FP32 = 0, LB_FP16_DEV = 1, LB_BF16_DEV = 2 } lb_precision;
 
 /* Time-stepping kernel. FUSED: one pass per step (pull streaming, densities
  * of the tile and its halo on chip, force, collision, store) -- the paper's
- * fused approach (Sec. 5.1). TWO_PASS: a density pass then a
- * stream + force + collide pass -- the paper's plain approach. */
-typedef enum { LB_KERNEL_FUSED = 0, LB_KERNEL_TWO_PASS = 1 } lb_kernel;
+ * fused approach (Sec. 5.1) -- fed by an asynchronous copy pipeline through
+ * shared memory. TWO_PASS: a density pass then a stream + force + collide
+ * pass -- the paper's plain approach. FUSED_REG: the fused step with a
+ * register double buffer instead of the copy pipeline (same arithmetic, same
+ * results bit for bit). */
+typedef enum { LB_KERNEL_FUSED = 0, LB_KERNEL_TWO_PASS = 1, LB_KERNEL_FUSED_REG = 2 } lb_kernel;
 
 typedef struct {
     int prec;              /* lb_precision (default LB_FP32) */

@@ -10,7 +10,7 @@ from . import build as _build
 
 LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_ENONFINITE, LB_ESTATE, LB_ETIMEOUT = range(7)
 PRECISIONS = {"fp32": 0, "fp16": 1, "bf16": 2}
-KERNELS = {"fused": 0, "two_pass": 1}
+KERNELS = {"fused": 0, "two_pass": 1, "fused_reg": 2}
 
 
 class LbOptions(ctypes.Structure):

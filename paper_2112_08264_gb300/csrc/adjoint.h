@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "kernels.h"
 
 namespace lbgb {
 
@@ -45,6 +46,7 @@ struct AdjointRun {
     double* red_part;       // kRedBlocks * kRedVals doubles
     double* red_out;
     int zsplit;
+    AsyncPlan plan;
 };
 
 size_t adjoint_workspace_bytes(int nx, int ny, int nz, int K);

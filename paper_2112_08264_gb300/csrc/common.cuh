@@ -105,7 +105,8 @@ __device__ __forceinline__ void sums(const float (&d)[2][Q], float& dA, float& d
 // F^A = -G psi^A SB + rho^A g, so tau F^A / rho^A = tau (-G SB + g) at a
 // fluid node (psi = rho there).
 // Equilibrium deviation: f^eq_i - w_i rho0 = w_i [(rho - rho0) + rho (3 c.u
-// + 4.5 (c.u)^2 - 1.5 u.u)] (Eq. LEQ with c_s^2 = 1/3).
+// + 4.5 (c.u)^2 - 1.5 u.u)] (Eq. LEQ with c_s^2 = 1/3); the stored value is
+// (1 - omega) d_i + omega (f^eq_i - w_i rho0).
 template <typename S>
 __device__ __forceinline__ void collide_store(const float (&d)[2][Q], const Phys& p, float dA, float dB,
                                               const float (&j)[3], const float (&SA)[3],
@@ -114,6 +115,7 @@ __device__ __forceinline__ void collide_store(const float (&d)[2][Q], const Phys
     const float rA = p.rho0[0] + dA, rB = p.rho0[1] + dB;
     const float inv = 1.0f / (rA + rB);
     const float up[3] = {j[0] * inv, j[1] * inv, j[2] * inv};
+    const float om1 = 1.0f - p.omega;
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const float (&Sk)[3] = (k == 0) ? SB : SA;
@@ -123,15 +125,28 @@ __device__ __forceinline__ void collide_store(const float (&d)[2][Q], const Phys
 #pragma unroll
         for (int a = 0; a < 3; ++a) u[a] = up[a] + p.tau * (p.g[a] - p.G * Sk[a]);
         const float uu15 = 1.5f * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-        static_for<0, Q>([&](auto I) {
-            constexpr int i = decltype(I)::value;
+        // omega * f^eq deviation, split for an opposite pair (i, i+1) into a
+        // part even in c (w (drho + rho (4.5 (c.u)^2 - 1.5 u.u))) and a part
+        // odd in c (3 w rho c.u)
+        const float wr1 = p.omega * (1.0f / 18.0f) * rk, wd1 = p.omega * (1.0f / 18.0f) * drk;
+        const float wr2 = p.omega * (1.0f / 36.0f) * rk, wd2 = p.omega * (1.0f / 36.0f) * drk;
+        S* out = dst + (size_t)(k * Q) * (size_t)g.N + (size_t)own;
+        {
+            const float eq0 = p.omega * (1.0f / 3.0f) * (drk - rk * uu15);
+            Store<S>::st(out, om1 * d[k][0] + eq0);
+        }
+        static_for<0, 9>([&](auto M) {
+            constexpr int i = 2 * decltype(M)::value + 1;   // (i, i + 1) opposite
             float cu = 0.f;
             if constexpr (Vel<i>::x != 0) cu += Vel<i>::x * u[0];
             if constexpr (Vel<i>::y != 0) cu += Vel<i>::y * u[1];
             if constexpr (Vel<i>::z != 0) cu += Vel<i>::z * u[2];
-            const float deq = wgt<i>() * (drk + rk * (cu * (3.0f + 4.5f * cu) - uu15));
-            const float out = d[k][i] - p.omega * (d[k][i] - deq);
-            Store<S>::st(dst + (size_t)(k * Q + i) * (size_t)g.N + (size_t)own, out);
+            constexpr bool axis = Vel<i>::c2 == 1;
+            const float wr = axis ? wr1 : wr2, wd = axis ? wd1 : wd2;
+            const float even = wr * (4.5f * cu * cu - uu15) + wd;
+            const float odd = 3.0f * wr * cu;
+            Store<S>::st(out + (size_t)i * g.N, om1 * d[k][i] + (even + odd));
+            Store<S>::st(out + (size_t)(i + 1) * g.N, om1 * d[k][i + 1] + (even - odd));
         });
     }
 }

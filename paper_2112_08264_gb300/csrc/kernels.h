@@ -9,10 +9,24 @@
 
 namespace lbgb {
 
+// Launch plan of the asynchronous-copy fused kernel (lb_fused_async.cu).
+struct AsyncPlan {
+    int ncols;      // tiles along x (32 columns each)
+    int R;          // tiles along y; tile cy covers [cy*ny/R, (cy+1)*ny/R)
+    int tymax;      // tallest tile (rows)
+    int zsplit;     // z-chunks per tile column
+    int zchunk;     // planes per z-chunk
+    int nst;        // copy stages in shared memory
+    int threads;    // 32 * tymax
+    int ns;         // copy slots per stage (own nodes + halo nodes)
+    size_t smem;    // dynamic shared memory per block
+    int box;        // 1: box copies (nx a multiple of the 16-byte chunk), 0: per-node copies
+};
+
 // One time step: src (post-collision state) -> dst.
 struct StepLaunch {
     int prec;                 // 0 fp32, 1 fp16 deviation, 2 bf16 deviation
-    int kernel;               // 0 fused, 1 two-pass
+    int kernel;               // 0 fused (async copies), 1 two-pass, 2 fused (register double buffer)
     const void* src;
     void* dst;
     const uint32_t* flags;    // nullptr = no solid nodes
@@ -20,13 +34,18 @@ struct StepLaunch {
     float* rho_out;           // optional: density deviations psi - rho0 of the source state, 2N
     Geom g;
     Phys p;
-    int zsplit;               // fused: z-chunks per tile column
+    int zsplit;               // register fused kernel: z-chunks per tile column
+    AsyncPlan plan;           // async fused kernel
 };
 
 cudaError_t launch_step(const StepLaunch& L, cudaStream_t st);
 
-// Fused-kernel launch geometry for a grid on a device with sm_count SMs.
+// Register fused kernel: launch geometry for a grid on a device with sm_count SMs.
 void fused_geometry(int nx, int ny, int nz, int sm_count, int* tiles, int* zsplit, int* threads);
+
+// Async fused kernel: plan for a grid, and its launcher (called by launch_step).
+AsyncPlan plan_fused_async(int nx, int ny, int nz, int sm_count, int prec, bool masked, size_t smem_limit);
+cudaError_t launch_fused_async(const StepLaunch& L, cudaStream_t st);
 
 // Solid flags from a device mask (1 = solid).
 cudaError_t launch_flags(const uint8_t* mask, uint32_t* flags, const Geom& g, cudaStream_t st);

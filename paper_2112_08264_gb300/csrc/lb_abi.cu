@@ -53,7 +53,7 @@ bool valid_dims(int nx, int ny, int nz) {
 
 bool valid_options(const lb_options& o) {
     if (o.prec < LB_FP32 || o.prec > LB_BF16_DEV) return false;
-    if (o.kernel < LB_KERNEL_FUSED || o.kernel > LB_KERNEL_TWO_PASS) return false;
+    if (o.kernel < LB_KERNEL_FUSED || o.kernel > LB_KERNEL_FUSED_REG) return false;
     if (!std::isfinite(o.rho0_A) || !std::isfinite(o.rho0_B)) return false;
     for (double g : o.body_force)
         if (!std::isfinite(g)) return false;
@@ -105,6 +105,7 @@ struct lb_ctx {
     bool initialized;
     long long steps;
     int sm_count, tiles, zsplit, threads;
+    AsyncPlan plan;
     // recording for the adjoint
     bool recording;       // lb_init was called with ckpt_every > 0 and the run is intact
     double rho0_d[2];
@@ -174,9 +175,10 @@ lb_status lb_create(int nx, int ny, int nz, float tau, float G, const uint8_t* m
     const Layout L = make_layout(nx, ny, nz, o);
     if (ws_bytes < L.total) return LB_ENOMEM;
 
-    int dev = 0, sms = 0;
+    int dev = 0, sms = 0, smem_optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return cuda_status("device query", e);
 
     lb_ctx* c = new (std::nothrow) lb_ctx();
@@ -202,6 +204,11 @@ lb_status lb_create(int nx, int ny, int nz, float tau, float G, const uint8_t* m
     c->has_mask = mask != nullptr;
     c->sm_count = sms;
     fused_geometry(nx, ny, nz, sms, &c->tiles, &c->zsplit, &c->threads);
+    c->plan = plan_fused_async(nx, ny, nz, sms, o.prec, mask != nullptr, (size_t)smem_optin);
+    if (o.kernel == LB_KERNEL_FUSED && c->plan.nst < 2) {   // no tile fits in shared memory
+        delete c;
+        return LB_EINVAL;
+    }
 
     if (mask) {
         e = cudaMemcpyAsync(c->mask_dev, mask, (size_t)c->g.N, cudaMemcpyHostToDevice, c->stream);
@@ -260,6 +267,7 @@ lb_status lb_step(lb_ctx* c, int n) {
     S.g = c->g;
     S.p = c->p;
     S.zsplit = c->zsplit;
+    S.plan = c->plan;
     for (int t = 0; t < n; ++t) {
         S.src = c->pop[c->cur];
         S.dst = c->pop[1 - c->cur];
@@ -334,6 +342,7 @@ lb_status lb_backward(lb_ctx* c, const float* dLA, const float* dLB, float* gA, 
     R.red_part = c->red_part;
     R.red_out = c->red_out;
     R.zsplit = c->zsplit;
+    R.plan = c->plan;
     R.kernel = c->opt.kernel;
     double gG_host = 0.0;
     cudaError_t e = run_adjoint(R, dLA, dLB, gA, gB, &gG_host, c->stream);
@@ -344,10 +353,13 @@ lb_status lb_backward(lb_ctx* c, const float* dLA, const float* dLB, float* gA, 
 
 lb_status lb_launch_info(const lb_ctx* c, int* launches, int* blocks, int* threads, int* zsplit) {
     if (!c) return LB_EINVAL;
-    if (launches) *launches = c->opt.kernel == LB_KERNEL_FUSED ? 1 : 2;
-    if (blocks) *blocks = c->opt.kernel == LB_KERNEL_FUSED ? c->tiles * c->zsplit : (int)((c->g.N + 255) / 256);
-    if (threads) *threads = c->opt.kernel == LB_KERNEL_FUSED ? c->threads : 256;
-    if (zsplit) *zsplit = c->zsplit;
+    const int k = c->opt.kernel;
+    if (launches) *launches = k == LB_KERNEL_TWO_PASS ? 2 : 1;
+    if (blocks)
+        *blocks = k == LB_KERNEL_FUSED ? c->plan.ncols * c->plan.R * c->plan.zsplit
+                : k == LB_KERNEL_FUSED_REG ? c->tiles * c->zsplit : (int)((c->g.N + 255) / 256);
+    if (threads) *threads = k == LB_KERNEL_FUSED ? c->plan.threads : k == LB_KERNEL_FUSED_REG ? c->threads : 256;
+    if (zsplit) *zsplit = k == LB_KERNEL_FUSED ? c->plan.zsplit : c->zsplit;
     return LB_OK;
 }
 

@@ -297,6 +297,7 @@ cudaError_t run_adjoint(const AdjointRun& R, const float* dLA, const float* dLB,
     S.g = R.g;
     S.p = R.p;
     S.zsplit = R.zsplit;
+    S.plan = R.plan;
     for (long long m = M - 1; m >= 0; --m) {
         const int Lm = (int)((T - m * R.K) < R.K ? (T - m * R.K) : R.K);
         if ((e = cudaMemcpyAsync(R.seg, R.ckpt + (size_t)m * R.state_bytes, R.state_bytes,

@@ -1,0 +1,530 @@
+// lb_fused_async.cu -- the fused step with an asynchronous copy pipeline.
+//
+// Same arithmetic as the register fused kernel (pull, densities, Shan-Chen
+// force, velocity shift, BGK, store; Eq. bgk, Eq. LEQ, Eq. LADDFLBE at rest),
+// restructured so that DRAM latency is hidden by copies in flight instead of
+// resident warps:
+//   - one block per SM owns a tile of 32 x TY x-y columns (TY chosen per grid
+//     so that the number of tiles is close to a multiple of the SM count) and
+//     marches along z;
+//   - every thread copies, with cp.async, exactly the values it will read
+//     later: the 38 pulled populations of its own node (streaming or
+//     bounce-back source) and, for the first threads, of one node of the
+//     one-node halo ring around the tile. A thread reads only its own copies,
+//     so the shared-memory stages need no barrier; NST stages keep NST planes
+//     of copies in flight;
+//   - per plane, each thread turns its landed copies into density deviations
+//     (own node and halo node) in a 4-plane ring, keeps its own populations in
+//     registers, and after one barrier collides the previous plane with the 18
+//     neighbour densities from the ring.
+// 16-bit storage: each copy fetches the aligned 32-bit word holding the
+// element; a per-node bit mask records which half is the element.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace lbgb {
+
+namespace {
+
+constexpr int kTX = 32;
+constexpr int kMaxTY = 16;
+
+__device__ __forceinline__ int wrap_any(int a, int n) {
+    a %= n;
+    return a < 0 ? a + n : a;
+}
+
+__device__ __forceinline__ void cp_async4(uint32_t saddr, const void* gptr) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(saddr), "l"(gptr) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void cp_wait_n(int n) {
+    switch (n) {
+        case 0: cp_wait<0>(); break;
+        case 1: cp_wait<1>(); break;
+        case 2: cp_wait<2>(); break;
+        default: cp_wait<3>(); break;
+    }
+}
+
+template <typename S> struct Word {
+    // 4-byte source address of element pointer p, and which 16-bit half holds it
+    static __device__ __forceinline__ const void* addr(const S* p) { return p; }
+    static __device__ __forceinline__ unsigned half(const S*) { return 0u; }
+    static __device__ __forceinline__ float value(uint32_t w, unsigned) { return __uint_as_float(w); }
+};
+template <> struct Word<__half> {
+    static __device__ __forceinline__ const void* addr(const __half* p) {
+        return reinterpret_cast<const void*>(reinterpret_cast<uintptr_t>(p) & ~(uintptr_t)3);
+    }
+    static __device__ __forceinline__ unsigned half(const __half* p) {
+        return (unsigned)((reinterpret_cast<uintptr_t>(p) >> 1) & 1u);
+    }
+    static __device__ __forceinline__ float value(uint32_t w, unsigned h) {
+        return __half2float(__ushort_as_half((unsigned short)(w >> (16u * h))));
+    }
+};
+template <> struct Word<__nv_bfloat16> {
+    static __device__ __forceinline__ const void* addr(const __nv_bfloat16* p) {
+        return reinterpret_cast<const void*>(reinterpret_cast<uintptr_t>(p) & ~(uintptr_t)3);
+    }
+    static __device__ __forceinline__ unsigned half(const __nv_bfloat16* p) {
+        return (unsigned)((reinterpret_cast<uintptr_t>(p) >> 1) & 1u);
+    }
+    static __device__ __forceinline__ float value(uint32_t w, unsigned h) {
+        return __bfloat162float(__ushort_as_bfloat16((unsigned short)(w >> (16u * h))));
+    }
+};
+
+struct Smem {
+    uint32_t* stage;            // [nst][38][ns] words
+    float2* ring;               // [4][tymax + 2][kTX + 2]
+    uint32_t* sflag;            // [nst][ns] flag words of the copied nodes
+    unsigned long long* shalf;  // [nst][ns] half-select bits (16-bit storage)
+};
+
+// Issue the copies of node (x, y, z) into slot `slot` of stage `st`; records
+// its flag word and half-select bits. Solid nodes copy nothing.
+template <typename S, bool MASK>
+__device__ __forceinline__ void issue_node(const S* __restrict__ src, const uint32_t* __restrict__ flags,
+                                           const Geom& g, const AsyncPlan& P, const Smem& sm, int st, int slot,
+                                           int x, int y, int z) {
+    PullIdx I;
+    pull_indices(g, x, y, z, I);
+    uint32_t fl = 0;
+    if constexpr (MASK) {
+        fl = __ldg(flags + I.own);
+        sm.sflag[st * P.ns + slot] = fl;
+        if (fl & kSolid) return;
+    }
+    unsigned long long hb = 0ull;
+    uint32_t* base = sm.stage + (size_t)st * 2 * Q * P.ns + slot;
+    static_for<0, Q>([&](auto II) {
+        constexpr int i = decltype(II)::value;
+        int idx = I.src[i];
+        int pop = i;
+        if constexpr (MASK && i != 0) {
+            if (fl & (1u << i)) { idx = I.own; pop = Vel<i>::opp; }
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const S* ep = src + (size_t)(k * Q + pop) * (size_t)g.N + (size_t)idx;
+            cp_async4((uint32_t)__cvta_generic_to_shared(base + (size_t)(k * Q + i) * P.ns), Word<S>::addr(ep));
+            hb |= (unsigned long long)Word<S>::half(ep) << (k * Q + i);
+        }
+    });
+    if constexpr (sizeof(S) == 2) sm.shalf[st * P.ns + slot] = hb;
+}
+
+// Read the landed copies of a slot into d (deviations) and return the
+// density deviations; solid nodes give (-rho0^A, -rho0^B).
+template <typename S, bool MASK>
+__device__ __forceinline__ float2 consume_node(const AsyncPlan& P, const Smem& sm, const Phys& p, int st, int slot,
+                                               float (&d)[2][Q], bool& solid) {
+    solid = false;
+    if constexpr (MASK) {
+        solid = (sm.sflag[st * P.ns + slot] & kSolid) != 0u;
+        if (solid) return make_float2(-p.rho0[0], -p.rho0[1]);
+    }
+    unsigned long long hb = 0ull;
+    if constexpr (sizeof(S) == 2) hb = sm.shalf[st * P.ns + slot];
+    const uint32_t* base = sm.stage + (size_t)st * 2 * Q * P.ns + slot;
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+            d[k][i] = Word<S>::value(base[(size_t)(k * Q + i) * P.ns], (unsigned)((hb >> (k * Q + i)) & 1ull));
+    return make_float2(dens_sum(d[0]), dens_sum(d[1]));
+}
+
+template <typename S, bool MASK>
+__global__ void __launch_bounds__(kTX * kMaxTY, 1)
+fused_async_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t* __restrict__ flags,
+                   float* __restrict__ rho_out, Geom g, Phys p, AsyncPlan P) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem sm;
+    sm.stage = reinterpret_cast<uint32_t*>(smem_raw);
+    sm.ring = reinterpret_cast<float2*>(sm.stage + (size_t)P.nst * 2 * Q * P.ns);
+    sm.sflag = reinterpret_cast<uint32_t*>(sm.ring + 4 * (P.tymax + 2) * (kTX + 2));
+    sm.shalf = reinterpret_cast<unsigned long long*>(sm.sflag + (MASK ? P.nst * P.ns : 0));
+    const int RW = kTX + 2, RH = P.tymax + 2;
+    auto ring_at = [&](int slot, int ly, int lx) -> float2& { return sm.ring[(slot * RH + ly + 1) * RW + lx + 1]; };
+
+    const int t = threadIdx.x, tx = t & 31, ty = t >> 5;
+    const int cx = blockIdx.x % P.ncols, cy = blockIdx.x / P.ncols;
+    const int x0 = cx * kTX;
+    const int y0 = (int)(((long long)cy * g.ny) / P.R);
+    const int y1 = (int)(((long long)(cy + 1) * g.ny) / P.R);
+    const int TYt = y1 - y0;
+    const int z0 = blockIdx.y * P.zchunk;
+    const int z1 = min(z0 + P.zchunk, g.nz);
+    if (z0 >= z1) return;   // uniform over the block
+    const int L = (z1 - z0) + 2;   // planes z0 - 1 .. z1
+
+    const bool own_row = ty < TYt;
+    const int gx = wrap_any(x0 + tx, g.nx);
+    const int gy = own_row ? y0 + ty : y0;
+    const bool active = own_row && (x0 + tx < g.nx);
+
+    const int nh = 2 * RW + 2 * TYt;
+    const bool has_halo = t < nh;
+    int hlx = 0, hly = 0;
+    if (t < RW) { hlx = t - 1; hly = -1; }
+    else if (t < 2 * RW) { hlx = t - RW - 1; hly = TYt; }
+    else if (t < 2 * RW + TYt) { hlx = -1; hly = t - 2 * RW; }
+    else { hlx = kTX; hly = t - 2 * RW - TYt; }
+    const int hgx = wrap_any(x0 + hlx, g.nx), hgy = wrap_any(y0 + hly, g.ny);
+    const int own_slot = t, halo_slot = P.threads + t;
+
+    auto plane_of = [&](int e) { return wrap_any(z0 - 1 + e, g.nz); };
+    auto issue = [&](int e) {
+        if (e < L) {
+            const int z = plane_of(e), st = e % P.nst;
+            if (own_row) issue_node<S, MASK>(src, flags, g, P, sm, st, own_slot, gx, gy, z);
+            if (has_halo) issue_node<S, MASK>(src, flags, g, P, sm, st, halo_slot, hgx, hgy, z);
+        }
+        cp_commit();   // one group per event, possibly empty, keeps the count uniform
+    };
+
+    for (int e = 0; e < P.nst; ++e) issue(e);
+
+    float cur[2][Q], nxt[2][Q];
+    bool solid_cur = true;
+    for (int e = 0; e < L; ++e) {
+        cp_wait_n(P.nst - 1);   // this thread's copies of event e have landed
+        const int st = e % P.nst, slot = e & 3;
+        bool solid_nxt = true;
+        if (own_row) ring_at(slot, ty, tx) = consume_node<S, MASK>(P, sm, p, st, own_slot, nxt, solid_nxt);
+        if (has_halo) {
+            float dh[2][Q];
+            bool sh;
+            ring_at(slot, hly, hlx) = consume_node<S, MASK>(P, sm, p, st, halo_slot, dh, sh);
+        }
+        __syncthreads();   // ring of plane e complete (and every reader of it done)
+        issue(e + P.nst);  // refill this thread's own slots of stage st
+        if (e >= 2 && active) {
+            const int z = plane_of(e - 1);
+            const long long own = gx + (long long)g.nx * (gy + (long long)g.ny * z);
+            const int sm_m = (e - 2) & 3, sm_c = (e - 1) & 3, sm_p = e & 3;
+            if (rho_out != nullptr) {
+                const float2 r = ring_at(sm_c, ty, tx);
+                rho_out[own] = r.x;
+                rho_out[g.N + own] = r.y;
+            }
+            if (!solid_cur) {
+                float dA, dB, j[3];
+                sums(cur, dA, dB, j);
+                float SA[3], SB[3];
+                neighbour_sums(
+                    [&](int dx, int dy, int dz) {
+                        const int s = dz < 0 ? sm_m : (dz > 0 ? sm_p : sm_c);
+                        return ring_at(s, ty + dy, tx + dx);
+                    },
+                    SA, SB);
+                collide_store<S>(cur, p, dA, dB, j, SA, SB, dst, g, (int)own);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+            for (int i = 0; i < Q; ++i) cur[k][i] = nxt[k][i];
+        solid_cur = solid_nxt;
+    }
+    cp_wait<0>();
+}
+
+// ---------------------------------------------------------------------------
+// Box variant (used when nx is a multiple of the 16-byte chunk width): per
+// plane and population the block copies one box of rows -- the tile and its
+// halo shifted by -c_i -- in 16-byte chunks, cooperatively, each chunk's
+// source wrapped periodically on its own (a chunk never straddles the wrap
+// since nx and the tile origin are multiples of the chunk width). A stage is
+// laid out [box row][population][column], so the pulled value of node
+// (lx, ly) for population (k, i) sits at row ly + 1, column lx + PAD - c_ix:
+// one shared-memory load at a compile-time offset from a per-node base.
+
+template <typename S> struct BoxGeo {
+    static constexpr int CW = 16 / (int)sizeof(S);   // elements per 16-byte chunk
+    static constexpr int PAD = CW;                   // box columns left of the tile
+    static constexpr int BW = kTX + 2 * PAD;         // box width (elements)
+    static constexpr int CPR = BW / CW;              // chunks per box row
+    static constexpr int ROW = 2 * Q * BW;           // stage row stride (elements)
+};
+
+__device__ __forceinline__ void cp_async16(uint32_t saddr, const void* gptr) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(gptr) : "memory");
+}
+
+template <typename S, bool MASK>
+__global__ void __launch_bounds__(kTX * kMaxTY, 1)
+fused_box_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t* __restrict__ flags,
+                 float* __restrict__ rho_out, Geom g, Phys p, AsyncPlan P) {
+    using B = BoxGeo<S>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int RH = P.tymax + 2, RW = kTX + 2;
+    const size_t pop_bytes = (size_t)RH * B::ROW * sizeof(S);
+    const size_t stage_bytes = pop_bytes + (MASK ? (size_t)RH * 40 * 4 : 0);
+    auto stage_base = [&](int st) -> S* { return reinterpret_cast<S*>(smem_raw + (size_t)st * stage_bytes); };
+    auto stage_flags = [&](int st) -> uint32_t* {
+        return reinterpret_cast<uint32_t*>(smem_raw + (size_t)st * stage_bytes + pop_bytes);
+    };
+    float2* ring = reinterpret_cast<float2*>(smem_raw + (size_t)P.nst * stage_bytes);
+    auto ring_at = [&](int slot, int ly, int lx) -> float2& { return ring[(slot * RH + ly + 1) * RW + lx + 1]; };
+
+    const int t = threadIdx.x, tx = t & 31, ty = t >> 5;
+    const int cx = blockIdx.x % P.ncols, cy = blockIdx.x / P.ncols;
+    const int x0 = cx * kTX;
+    const int y0 = (int)(((long long)cy * g.ny) / P.R);
+    const int y1 = (int)(((long long)(cy + 1) * g.ny) / P.R);
+    const int TYt = y1 - y0;
+    const int z0 = blockIdx.y * P.zchunk;
+    const int z1 = min(z0 + P.zchunk, g.nz);
+    if (z0 >= z1) return;
+    const int L = (z1 - z0) + 2;
+
+    const bool own_row = ty < TYt;
+    const int gx = wrap_any(x0 + tx, g.nx);
+    const int gy = own_row ? y0 + ty : y0;
+    const bool active = own_row && (x0 + tx < g.nx);
+    const int nh = 2 * RW + 2 * TYt;
+    const bool has_halo = t < nh;
+    int hlx = 0, hly = 0;
+    if (t < RW) { hlx = t - 1; hly = -1; }
+    else if (t < 2 * RW) { hlx = t - RW - 1; hly = TYt; }
+    else if (t < 2 * RW + TYt) { hlx = -1; hly = t - 2 * RW; }
+    else { hlx = kTX; hly = t - 2 * RW - TYt; }
+    const int hgx = wrap_any(x0 + hlx, g.nx), hgy = wrap_any(y0 + hly, g.ny);
+
+    auto plane_of = [&](int e) { return wrap_any(z0 - 1 + e, g.nz); };
+
+    // Copier thread t (< RH * CPR) owns chunk (row jr, column jc) of all 38
+    // boxes. Its wrapped source offsets within a plane depend only on c_iy
+    // and are computed once; on masked grids threads t < RH * 10 also copy
+    // one 4-word chunk of the flag box.
+    const bool copier = t < RH * B::CPR;
+    const int jr = t / B::CPR, jc = t - (t / B::CPR) * B::CPR;
+    const int xs_chunk = wrap_any(x0 - B::PAD + jc * B::CW, g.nx);
+    const int yoff_m = wrap_any(y0 + jr, g.ny) * g.nx + xs_chunk;       // c_iy = -1
+    const int yoff_0 = wrap_any(y0 - 1 + jr, g.ny) * g.nx + xs_chunk;   // c_iy =  0
+    const int yoff_p = wrap_any(y0 - 2 + jr, g.ny) * g.nx + xs_chunk;   // c_iy = +1
+    const int sdst = jr * B::ROW + jc * B::CW;
+    const bool fcopier = MASK && t < RH * 10;
+    int foff = 0, fdst = 0;
+    if (fcopier) {
+        const int fr = t / 10, fc = t - (t / 10) * 10;
+        foff = wrap_any(y0 - 1 + fr, g.ny) * g.nx + wrap_any(x0 - 4 + fc * 4, g.nx);
+        fdst = fr * 40 + fc * 4;
+    }
+
+    auto issue = [&](int e) {
+        if (e < L) {
+            const int z = plane_of(e), st = e % P.nst;
+            if (copier) {
+                // plane offsets for c_iz = -1, 0, +1 (source plane z - c_iz)
+                const size_t pz_m = (size_t)wrap_inc(z, g.nz) * g.plane;
+                const size_t pz_0 = (size_t)z * g.plane;
+                const size_t pz_p = (size_t)wrap_dec(z, g.nz) * g.plane;
+                const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(stage_base(st) + sdst);
+                static_for<0, 2 * Q>([&](auto PP) {
+                    constexpr int pop = decltype(PP)::value;
+                    constexpr int i = pop % Q;
+                    const size_t pz = Vel<i>::z < 0 ? pz_m : (Vel<i>::z > 0 ? pz_p : pz_0);
+                    const int yo = Vel<i>::y < 0 ? yoff_m : (Vel<i>::y > 0 ? yoff_p : yoff_0);
+                    cp_async16(sbase + pop * B::BW * (int)sizeof(S), src + (size_t)pop * g.N + pz + yo);
+                });
+            }
+            if constexpr (MASK) {
+                if (fcopier)
+                    cp_async16((uint32_t)__cvta_generic_to_shared(stage_flags(st) + fdst),
+                               flags + (size_t)z * g.plane + foff);
+            }
+        }
+        cp_commit();
+    };
+
+    // pulled deviations of node (lx, ly) at plane z from stage st
+    auto read_node = [&](int st, int lx, int ly, int x, int y, int z, float (&d)[2][Q], bool& solid) -> float2 {
+        uint32_t fl = 0;
+        solid = false;
+        if constexpr (MASK) {
+            fl = stage_flags(st)[(ly + 1) * 40 + lx + 4];
+            solid = (fl & kSolid) != 0u;
+            if (solid) return make_float2(-p.rho0[0], -p.rho0[1]);
+        }
+        const S* nb = stage_base(st) + (ly + 1) * B::ROW + lx + B::PAD;
+        static_for<0, Q>([&](auto II) {
+            constexpr int i = decltype(II)::value;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                if constexpr (MASK && i != 0) {
+                    if (fl & (1u << i)) {   // bounce-back: own node, opposite population
+                        const size_t own = (size_t)x + (size_t)g.nx * ((size_t)y + (size_t)g.ny * z);
+                        d[k][i] = Store<S>::ld(src + (size_t)(k * Q + Vel<i>::opp) * g.N + own);
+                        continue;
+                    }
+                }
+                d[k][i] = Store<S>::to_f(nb[(k * Q + i) * B::BW - Vel<i>::x]);
+            }
+        });
+        return make_float2(dens_sum(d[0]), dens_sum(d[1]));
+    };
+
+    for (int e = 0; e < P.nst; ++e) issue(e);
+
+    float cur[2][Q], nxt[2][Q];
+    bool solid_cur = true;
+    for (int e = 0; e < L; ++e) {
+        cp_wait_n(P.nst - 1);
+        __syncthreads();   // every thread's chunks of event e are visible
+        const int st = e % P.nst, slot = e & 3;
+        const int z = plane_of(e);
+        bool solid_nxt = true;
+        if (own_row) ring_at(slot, ty, tx) = read_node(st, tx, ty, gx, gy, z, nxt, solid_nxt);
+        if (has_halo) {
+            float dh[2][Q];
+            bool sh;
+            ring_at(slot, hly, hlx) = read_node(st, hlx, hly, hgx, hgy, z, dh, sh);
+        }
+        __syncthreads();   // ring of plane e complete; stage st fully read
+        issue(e + P.nst);
+        if (e >= 2 && active) {
+            const int zc = plane_of(e - 1);
+            const long long own = gx + (long long)g.nx * (gy + (long long)g.ny * zc);
+            const int sm_m = (e - 2) & 3, sm_c = (e - 1) & 3, sm_p = e & 3;
+            if (rho_out != nullptr) {
+                const float2 r = ring_at(sm_c, ty, tx);
+                rho_out[own] = r.x;
+                rho_out[g.N + own] = r.y;
+            }
+            if (!solid_cur) {
+                float dA, dB, j[3];
+                sums(cur, dA, dB, j);
+                float SA[3], SB[3];
+                neighbour_sums(
+                    [&](int dx, int dy, int dz) {
+                        const int s2 = dz < 0 ? sm_m : (dz > 0 ? sm_p : sm_c);
+                        return ring_at(s2, ty + dy, tx + dx);
+                    },
+                    SA, SB);
+                collide_store<S>(cur, p, dA, dB, j, SA, SB, dst, g, (int)own);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+            for (int i = 0; i < Q; ++i) cur[k][i] = nxt[k][i];
+        solid_cur = solid_nxt;
+    }
+    cp_wait<0>();
+}
+
+template <typename S, bool MASK>
+cudaError_t launch_box_t(const StepLaunch& L, cudaStream_t st) {
+    const AsyncPlan& P = L.plan;
+    auto kern = fused_box_kernel<S, MASK>;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    dim3 grid(P.ncols * P.R, P.zsplit, 1);
+    kern<<<grid, P.threads, P.smem, st>>>(static_cast<const S*>(L.src), static_cast<S*>(L.dst), L.flags, L.rho_out,
+                                          L.g, L.p, P);
+    return cudaGetLastError();
+}
+
+template <typename S, bool MASK>
+cudaError_t launch_t(const StepLaunch& L, cudaStream_t st) {
+    const AsyncPlan& P = L.plan;
+    auto kern = fused_async_kernel<S, MASK>;
+    static bool configured = false;   // the attribute is per function, not per device state
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    dim3 grid(P.ncols * P.R, P.zsplit, 1);
+    kern<<<grid, P.threads, P.smem, st>>>(static_cast<const S*>(L.src), static_cast<S*>(L.dst), L.flags, L.rho_out,
+                                          L.g, L.p, P);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_fused_async(const StepLaunch& L, cudaStream_t st) {
+    const bool m = L.flags != nullptr;
+    if (L.plan.box) {
+        switch (L.prec) {
+            case 0: return m ? launch_box_t<float, true>(L, st) : launch_box_t<float, false>(L, st);
+            case 1: return m ? launch_box_t<__half, true>(L, st) : launch_box_t<__half, false>(L, st);
+            case 2: return m ? launch_box_t<__nv_bfloat16, true>(L, st) : launch_box_t<__nv_bfloat16, false>(L, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    switch (L.prec) {
+        case 0: return m ? launch_t<float, true>(L, st) : launch_t<float, false>(L, st);
+        case 1: return m ? launch_t<__half, true>(L, st) : launch_t<__half, false>(L, st);
+        case 2: return m ? launch_t<__nv_bfloat16, true>(L, st) : launch_t<__nv_bfloat16, false>(L, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+AsyncPlan plan_fused_async(int nx, int ny, int nz, int sm_count, int prec, bool masked, size_t smem_limit) {
+    AsyncPlan best{};
+    double best_cost = 1e300;
+    const int ncols = (nx + kTX - 1) / kTX;
+    const int esize = prec == 0 ? 4 : 2;
+    const int cw = 16 / esize;
+    const bool box = (nx % cw) == 0 && (nx % 4) == 0;   // chunks of populations and of flag words
+    const int rmin = (ny + kMaxTY - 1) / kMaxTY;
+    for (int R = rmin; R <= ny; ++R) {
+        const int tymax = (ny + R - 1) / R;
+        if (tymax < 4 && R > rmin && ny >= 4) break;
+        const int threads = kTX * tymax;
+        const int ns = threads + 2 * (kTX + 2) + 2 * tymax;
+        if (threads < 2 * (kTX + 2) + 2 * tymax) continue;   // every halo node needs a thread
+        if (box && threads < (tymax + 2) * ((kTX + 2 * cw) / cw)) continue;   // a chunk per copier thread
+        const size_t stage = box ? (size_t)2 * Q * (tymax + 2) * (kTX + 2 * cw) * esize +
+                                       (masked ? (size_t)(tymax + 2) * 40 * 4 : 0)
+                                 : (size_t)2 * Q * ns * 4 + (masked ? (size_t)ns * 4 : 0) + (prec != 0 ? (size_t)ns * 8 : 0);
+        const size_t ring = (size_t)4 * (tymax + 2) * (kTX + 2) * 8;
+        if (smem_limit < ring + 2 * stage) continue;
+        int nst = (int)((smem_limit - ring) / stage);
+        nst = nst > 4 ? 4 : nst;
+        const long long bxy = (long long)ncols * R;
+        const int zs_max = nz / 4 > 1 ? nz / 4 : 1;
+        for (int zs = 1; zs <= zs_max; ++zs) {
+            const int zchunk = (nz + zs - 1) / zs;
+            const long long blocks = bxy * zs;
+            const long long waves = (blocks + sm_count - 1) / sm_count;
+            // per-block time ~ columns (own + 30% weight for halo nodes) x planes
+            // (+2 halo planes), and blocks of few warps hide latency worse
+            const double work = (tymax + 0.3 * (2.0 * (kTX + 2) + 2.0 * tymax) / kTX) * (zchunk + 2);
+            const double cost = waves * work * (1.0 + 4.0 / tymax);
+            if (cost < best_cost * (1 - 1e-9)) {
+                best_cost = cost;
+                best.ncols = ncols;
+                best.R = R;
+                best.tymax = tymax;
+                best.zsplit = zs;
+                best.zchunk = zchunk;
+                best.nst = nst;
+                best.threads = threads;
+                best.ns = ns;
+                best.smem = ring + (size_t)nst * stage;
+                best.box = box ? 1 : 0;
+            }
+            if (blocks >= sm_count) break;   // more z-splits only add halo planes
+        }
+    }
+    return best;
+}
+
+}  // namespace lbgb

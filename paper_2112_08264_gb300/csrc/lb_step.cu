@@ -1,7 +1,9 @@
 // lb_step.cu -- time-step kernels.
 //
-// FUSED (the paper's fused approach, Sec. 5.1, redesigned for the Shan-Chen
-// force): one launch per step. The force at node x needs the post-streaming
+// FUSED, register double buffer (kernel 2; the default fused kernel is the
+// asynchronous-copy variant in lb_fused_async.cu, same arithmetic): the
+// paper's fused approach (Sec. 5.1), redesigned for the Shan-Chen force: one
+// launch per step. The force at node x needs the post-streaming
 // densities of its 18 neighbours, i.e. sums of populations pulled up to two
 // sites away, so a block owns a TX x TY tile of x-y columns and marches along
 // z. For each plane z+1 it pulls the 38 populations of its own columns (kept
@@ -182,7 +184,7 @@ template <typename S, bool MASK>
 cudaError_t launch_step_t(const StepLaunch& L, cudaStream_t st) {
     const S* src = static_cast<const S*>(L.src);
     S* dst = static_cast<S*>(L.dst);
-    if (L.kernel == 0) {
+    if (L.kernel == 2) {
         dim3 block(kTX, kTY, 1);
         dim3 grid((L.g.nx + kTX - 1) / kTX, (L.g.ny + kTY - 1) / kTY, L.zsplit);
         const int zchunk = (L.g.nz + L.zsplit - 1) / L.zsplit;
@@ -199,6 +201,7 @@ cudaError_t launch_step_t(const StepLaunch& L, cudaStream_t st) {
 }  // namespace
 
 cudaError_t launch_step(const StepLaunch& L, cudaStream_t st) {
+    if (L.kernel == 0) return launch_fused_async(L, st);
     const bool m = L.flags != nullptr;
     switch (L.prec) {
         case 0: return m ? launch_step_t<float, true>(L, st) : launch_step_t<float, false>(L, st);

@@ -18,7 +18,7 @@ template <> struct Store<float> {
     static constexpr int bytes = 4;
     static __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
     static __device__ __forceinline__ void st(float* p, float v) { __stcs(p, v); }
-    static __device__ __forceinline__ float to_float(float v) { return v; }
+    static __device__ __forceinline__ float to_f(float v) { return v; }
 };
 
 template <> struct Store<__half> {
@@ -29,6 +29,7 @@ template <> struct Store<__half> {
     static __device__ __forceinline__ void st(__half* p, float v) {
         __stcs(reinterpret_cast<unsigned short*>(p), __half_as_ushort(__float2half_rn(v)));
     }
+    static __device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
 };
 
 template <> struct Store<__nv_bfloat16> {
@@ -40,6 +41,7 @@ template <> struct Store<__nv_bfloat16> {
     static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) {
         __stcs(reinterpret_cast<unsigned short*>(p), __bfloat16_as_ushort(__float2bfloat16_rn(v)));
     }
+    static __device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
 };
 
 }  // namespace lbgb

@@ -125,7 +125,7 @@ def test_initial_state_matches_oracle(prec, masked):
         assert np.all(got[:, :, mask == 1] == 0)
 
 
-@pytest.mark.parametrize("kernel", ["fused", "two_pass"])
+@pytest.mark.parametrize("kernel", ["fused", "two_pass", "fused_reg"])
 @pytest.mark.parametrize("shape,masked,tau,G,g", [
     ((32, 32, 32), False, 1.0, 0.65, (0, 0, 0)),
     ((37, 21, 13), True, 0.8, 1.3, (1e-5, -2e-5, 3e-6)),
@@ -202,13 +202,17 @@ def test_velocity_dominated_flow_parity(kernel):
     assert err <= 1e-5 * scale
 
 
-def test_fused_and_two_pass_are_bitwise_equal():
-    nx, ny, nz = 40, 24, 18
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+@pytest.mark.parametrize("shape,masked", [((40, 24, 18), True), ((64, 48, 20), False), ((3, 3, 3), False)])
+def test_all_kernels_are_bitwise_equal(prec, shape, masked):
+    """The three step kernels do the same arithmetic in the same order."""
+    nx, ny, nz = shape
     rA, rB = inputs.spinodal(nx, ny, nz, seed=31)
-    mask = inputs.random_mask(nx, ny, nz, seed=32, solid_fraction=0.1)
-    a = gpu_run((nx, ny, nz), 10, 0.8, 1.1, rA, rB, mask=mask, kernel="fused").get_state()
-    b = gpu_run((nx, ny, nz), 10, 0.8, 1.1, rA, rB, mask=mask, kernel="two_pass").get_state()
-    assert torch.equal(a, b)
+    mask = inputs.random_mask(nx, ny, nz, seed=32, solid_fraction=0.1) if masked else None
+    ref = gpu_run(shape, 10, 0.8, 1.1, rA, rB, mask=mask, kernel="two_pass", prec=prec).get_state()
+    for kernel in ("fused", "fused_reg"):
+        got = gpu_run(shape, 10, 0.8, 1.1, rA, rB, mask=mask, kernel=kernel, prec=prec).get_state()
+        assert torch.equal(got, ref), kernel
 
 
 @pytest.mark.parametrize("prec,tol_rho", [("fp16", 2e-3), ("bf16", 2e-3)])
