@@ -19,6 +19,8 @@
 //   lambda^k_i(x) = (1 - omega) mu^k_i + c_i.W + q_k
 //                   + sum_{i'>=1} w_i' c_i'.sigma^k(x - c_i')
 // and dL/dG accumulates -tau (V_A.S^B + V_B.S^A) over nodes and steps.
+// The recompute keeps, per node, drho^A, drho^B, j, S^A and S^B (the forward
+// step's own values), so the reverse step never pulls f_t.
 #pragma once
 #include <cstddef>
 #include <cstdint>
@@ -46,10 +48,14 @@ struct AdjointRun {
     double* red_part;       // kRedBlocks * kRedVals doubles
     double* red_out;
     int zsplit;
-    AsyncPlan plan;
+    AsyncPlan plan;         // forward (recompute) plan
+    AsyncPlan adjplan;      // fused box adjoint plan; adjplan.box == 0: two-pass adjoint
 };
 
 size_t adjoint_workspace_bytes(int nx, int ny, int nz, int K);
+
+// Plan of the fused box adjoint (box = 0 when nx is not a multiple of 4).
+AsyncPlan plan_adjoint_box(int nx, int ny, int nz, int sm_count, bool masked, size_t smem_limit);
 
 cudaError_t run_adjoint(const AdjointRun& R, const float* dLA, const float* dLB, float* gA, float* gB,
                         double* gG, cudaStream_t st);

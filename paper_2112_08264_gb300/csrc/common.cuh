@@ -151,6 +151,17 @@ __device__ __forceinline__ void collide_store(const float (&d)[2][Q], const Phys
     }
 }
 
+// Per-node moments kept by the adjoint's recompute, 11 fields [c][s]:
+// drho^A, drho^B, j (3), S^A (3), S^B (3). Written at fluid nodes only.
+constexpr int kMom = 11;
+__device__ __forceinline__ void store_moments(float* __restrict__ mom, const Geom& g, long long own, float dA,
+                                              float dB, const float (&j)[3], const float (&SA)[3],
+                                              const float (&SB)[3]) {
+    const float v[kMom] = {dA, dB, j[0], j[1], j[2], SA[0], SA[1], SA[2], SB[0], SB[1], SB[2]};
+#pragma unroll
+    for (int c = 0; c < kMom; ++c) mom[(size_t)c * g.N + own] = v[c];
+}
+
 // Density deviations dpsi^k = psi^k - rho0^k of node (x, y, z): sum_i d_i^k at
 // a fluid node, -rho0^k at a solid node (psi = 0 there). Since
 // sum_{i>=1} w_i c_i = 0, the force sums S^k = sum_i w_i psi^k(x + c_i) c_i are

@@ -31,7 +31,7 @@ struct StepLaunch {
     void* dst;
     const uint32_t* flags;    // nullptr = no solid nodes
     float* rho;               // density scratch (two-pass), 2N floats
-    float* rho_out;           // optional: density deviations psi - rho0 of the source state, 2N
+    float* mom_out;           // optional: per-node moments of the source state (kMom x N, fluid nodes)
     Geom g;
     Phys p;
     int zsplit;               // register fused kernel: z-chunks per tile column

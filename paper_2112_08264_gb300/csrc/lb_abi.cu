@@ -106,6 +106,7 @@ struct lb_ctx {
     long long steps;
     int sm_count, tiles, zsplit, threads;
     AsyncPlan plan;
+    AsyncPlan adjplan;
     // recording for the adjoint
     bool recording;       // lb_init was called with ckpt_every > 0 and the run is intact
     double rho0_d[2];
@@ -209,6 +210,9 @@ lb_status lb_create(int nx, int ny, int nz, float tau, float G, const uint8_t* m
         delete c;
         return LB_EINVAL;
     }
+    c->adjplan = AsyncPlan{};
+    if (o.ckpt_every > 0)
+        c->adjplan = plan_adjoint_box(nx, ny, nz, sms, mask != nullptr, (size_t)smem_optin);
 
     if (mask) {
         e = cudaMemcpyAsync(c->mask_dev, mask, (size_t)c->g.N, cudaMemcpyHostToDevice, c->stream);
@@ -263,7 +267,7 @@ lb_status lb_step(lb_ctx* c, int n) {
     S.kernel = c->opt.kernel;
     S.flags = c->has_mask ? c->flags : nullptr;
     S.rho = c->rho;
-    S.rho_out = nullptr;
+    S.mom_out = nullptr;
     S.g = c->g;
     S.p = c->p;
     S.zsplit = c->zsplit;
@@ -343,6 +347,7 @@ lb_status lb_backward(lb_ctx* c, const float* dLA, const float* dLB, float* gA, 
     R.red_out = c->red_out;
     R.zsplit = c->zsplit;
     R.plan = c->plan;
+    R.adjplan = c->adjplan;
     R.kernel = c->opt.kernel;
     double gG_host = 0.0;
     cudaError_t e = run_adjoint(R, dLA, dLB, gA, gB, &gG_host, c->stream);

@@ -4,13 +4,17 @@
 // Backward over a recorded run of T steps with checkpoints every K steps:
 // for each segment, last to first, the forward step is re-run from its
 // checkpoint (the same kernel, so the same bits), keeping every state of the
-// segment and its density deviations; the adjoint then runs backwards through
-// the segment, two passes per step:
-//   pass A (per node): pull f_t, gather mu = P^T lambda_{t+1}, force sums from
-//           the stored densities; write W, q_k, sigma^k and a per-block FP64
-//           partial of dL/dG;
-//   pass B (per node): gather mu again, add the neighbour gather of sigma,
-//           write lambda_t.
+// segment and, per node, the moments the reverse step needs (drho^A, drho^B,
+// j, S^A, S^B). The adjoint then runs backwards through the segment:
+//   box kernel (nx a multiple of 4): one launch per reverse step; per plane
+//     the block copies boxes of lambda_{t+1} (shifted by +c_i, the transpose
+//     of the pull) and of the moments, computes sigma^k for its tile and
+//     halo into a 4-plane ring and, after one barrier, writes lambda_t of the
+//     previous plane with the neighbour gather of sigma;
+//   two-pass fallback: pass A writes W, q_k, sigma^k per node, pass B gathers.
+// dL/dG accumulates in FP64 per block and is summed in a fixed order.
+#include <cstdint>
+
 #include <cuda_runtime.h>
 
 #include "adjoint.h"
@@ -22,13 +26,14 @@ namespace lbgb {
 namespace {
 
 constexpr int kAux = 11;   // W[3], q[2], sigma^A[3], sigma^B[3]
+constexpr int kTX = 32;
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct AdjBufs {
     float* lam[2];
     float* aux;
-    float* segrho;
+    float* segmom;
     double* gacc;
 };
 
@@ -38,9 +43,14 @@ AdjBufs carve(char* adj, size_t N, int K) {
     b.lam[0] = reinterpret_cast<float*>(adj + off); off += a256(2 * Q * N * 4);
     b.lam[1] = reinterpret_cast<float*>(adj + off); off += a256(2 * Q * N * 4);
     b.aux = reinterpret_cast<float*>(adj + off); off += a256((size_t)kAux * N * 4);
-    b.segrho = reinterpret_cast<float*>(adj + off); off += a256((size_t)K * 2 * N * 4);
+    b.segmom = reinterpret_cast<float*>(adj + off); off += a256((size_t)K * kMom * N * 4);
     b.gacc = reinterpret_cast<double*>(adj + off);
     return b;
+}
+
+__device__ __forceinline__ int wrap_any(int a, int n) {
+    a %= n;
+    return a < 0 ? a + n : a;
 }
 
 __device__ __forceinline__ void site_xyz(long long s, const Geom& g, int& x, int& y, int& z) {
@@ -71,29 +81,14 @@ __device__ __forceinline__ void gather_mu(const float* __restrict__ lam, const G
     });
 }
 
-// Force sums S^k from stored density deviations (neighbours of node x).
-__device__ __forceinline__ void force_sums(const float* __restrict__ dpsi, const Geom& g, int x, int y, int z,
-                                           float (&SA)[3], float (&SB)[3]) {
-    neighbour_sums(
-        [&](int dx, int dy, int dz) {
-            const int xx = dx > 0 ? wrap_inc(x, g.nx) : (dx < 0 ? wrap_dec(x, g.nx) : x);
-            const int yy = dy > 0 ? wrap_inc(y, g.ny) : (dy < 0 ? wrap_dec(y, g.ny) : y);
-            const int zz = dz > 0 ? wrap_inc(z, g.nz) : (dz < 0 ? wrap_dec(z, g.nz) : z);
-            const long long t = xx + (long long)g.nx * (yy + (long long)g.ny * zz);
-            return make_float2(__ldg(dpsi + t), __ldg(dpsi + g.N + t));
-        },
-        SA, SB);
-}
-
-// Per-node adjoint quantities of the collision (see adjoint.h).
-__device__ __forceinline__ void adj_node(const float (&d)[2][Q], const float (&mu)[2][Q], const Phys& p,
-                                         const float (&SA)[3], const float (&SB)[3], float (&W)[3],
-                                         float (&q)[2], float (&sA)[3], float (&sB)[3], float& dG) {
-    float dA, dB, j[3];
-    sums(d, dA, dB, j);
-    const float rA = p.rho0[0] + dA, rB = p.rho0[1] + dB;
+// Per-node adjoint quantities of the collision (see adjoint.h) from the
+// forward moments (dA, dB, j, S^A, S^B) and the adjoint mu.
+__device__ __forceinline__ void adj_node(const float (&mo)[kMom], const float (&mu)[2][Q], const Phys& p,
+                                         float (&W)[3], float (&q)[2], float (&sA)[3], float (&sB)[3], float& dG) {
+    const float rA = p.rho0[0] + mo[0], rB = p.rho0[1] + mo[1];
     const float inv = 1.0f / (rA + rB);
-    const float up[3] = {j[0] * inv, j[1] * inv, j[2] * inv};
+    const float up[3] = {mo[2] * inv, mo[3] * inv, mo[4] * inv};
+    const float SA[3] = {mo[5], mo[6], mo[7]}, SB[3] = {mo[8], mo[9], mo[10]};
     float V[2][3], E[2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
@@ -137,11 +132,27 @@ __device__ __forceinline__ void adj_node(const float (&d)[2][Q], const float (&m
                    V[1][0] * SA[0] + V[1][1] * SA[1] + V[1][2] * SA[2]);
 }
 
-template <typename S, bool MASK>
+// local part of lambda_t: (1 - omega) mu_i + c_i . W + q_k, in place
+__device__ __forceinline__ void local_part(float (&mu)[2][Q], const Phys& p, const float (&W)[3],
+                                           const float (&q)[2]) {
+    const float om1 = 1.0f - p.omega;
+    static_for<0, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        float cW = 0.f;
+        if constexpr (Vel<i>::x != 0) cW += Vel<i>::x * W[0];
+        if constexpr (Vel<i>::y != 0) cW += Vel<i>::y * W[1];
+        if constexpr (Vel<i>::z != 0) cW += Vel<i>::z * W[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) mu[k][i] = om1 * mu[k][i] + cW + q[k];
+    });
+}
+
+// ---- two-pass fallback ----
+
+template <bool MASK>
 __global__ void __launch_bounds__(256)
-adj_pass_a(const S* __restrict__ gt, const float* __restrict__ dpsi, const float* __restrict__ lam,
-           const uint32_t* __restrict__ flags, float* __restrict__ aux, double* __restrict__ partials, Geom g,
-           Phys p) {
+adj_pass_a(const float* __restrict__ mom, const float* __restrict__ lam, const uint32_t* __restrict__ flags,
+           float* __restrict__ aux, double* __restrict__ partials, Geom g, Phys p) {
     double v[kRedVals] = {0, 0, 0, 0, 0, 0};
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.N; s += stride) {
@@ -154,15 +165,13 @@ adj_pass_a(const S* __restrict__ gt, const float* __restrict__ dpsi, const float
             for (int c = 0; c < kAux; ++c) aux[(size_t)c * g.N + s] = 0.f;
             continue;
         }
-        PullIdx P;
-        pull_indices(g, x, y, z, P);
-        float d[2][Q], mu[2][Q];
-        pull<S, MASK>(gt, g, P, fl, d);
+        float mu[2][Q];
         gather_mu<MASK>(lam, g, x, y, z, s, fl, mu);
-        float SA[3], SB[3];
-        force_sums(dpsi, g, x, y, z, SA, SB);
+        float mo[kMom];
+#pragma unroll
+        for (int c = 0; c < kMom; ++c) mo[c] = __ldg(mom + (size_t)c * g.N + s);
         float W[3], q[2], sA[3], sB[3], dG;
-        adj_node(d, mu, p, SA, SB, W, q, sA, sB, dG);
+        adj_node(mo, mu, p, W, q, sA, sB, dG);
         const float out[kAux] = {W[0], W[1], W[2], q[0], q[1], sA[0], sA[1], sA[2], sB[0], sB[1], sB[2]};
 #pragma unroll
         for (int c = 0; c < kAux; ++c) aux[(size_t)c * g.N + s] = out[c];
@@ -189,6 +198,7 @@ adj_pass_b(const float* __restrict__ lam_in, const float* __restrict__ aux, cons
     gather_mu<MASK>(lam_in, g, x, y, z, s, fl, mu);
     const float W[3] = {aux[s], aux[g.N + s], aux[2 * g.N + s]};
     const float q[2] = {aux[3 * g.N + s], aux[4 * g.N + s]};
+    local_part(mu, p, W, q);
     // h^k(x) = sum_{i>=1} w_i c_i . sigma^k(x - c_i)
     PullIdx P;
     pull_indices(g, x, y, z, P);
@@ -208,14 +218,211 @@ adj_pass_b(const float* __restrict__ lam_in, const float* __restrict__ aux, cons
     });
     static_for<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        float cW = 0.f;
-        if constexpr (Vel<i>::x != 0) cW += Vel<i>::x * W[0];
-        if constexpr (Vel<i>::y != 0) cW += Vel<i>::y * W[1];
-        if constexpr (Vel<i>::z != 0) cW += Vel<i>::z * W[2];
 #pragma unroll
-        for (int k = 0; k < 2; ++k)
-            lam_out[(size_t)(k * Q + i) * g.N + s] = (1.0f - p.omega) * mu[k][i] + cW + q[k] + h[k];
+        for (int k = 0; k < 2; ++k) lam_out[(size_t)(k * Q + i) * g.N + s] = mu[k][i] + h[k];
     });
+}
+
+// ---- fused box adjoint ----
+
+constexpr int kBW = 40;               // box width (floats): 4 left of the tile, 32, 4 right
+constexpr int kCPR = kBW / 4;         // 16-byte chunks per box row
+constexpr int kBoxes = 2 * Q + kMom;  // lambda populations + moment fields
+constexpr int kROW = kBoxes * kBW;    // stage row stride (floats)
+
+__device__ __forceinline__ void cp_async16(uint32_t saddr, const void* gptr) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(gptr) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void cp_wait_n(int n) {
+    switch (n) {
+        case 0: cp_wait<0>(); break;
+        case 1: cp_wait<1>(); break;
+        case 2: cp_wait<2>(); break;
+        default: cp_wait<3>(); break;
+    }
+}
+
+struct Sig {
+    float a[3], b[3];
+};
+
+template <bool MASK>
+__global__ void __launch_bounds__(512, 1)
+adj_box_kernel(const float* __restrict__ lam_in, const float* __restrict__ mom, const uint32_t* __restrict__ flags,
+               float* __restrict__ lam_out, double* __restrict__ partials, Geom g, Phys p, AsyncPlan P) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int RH = P.tymax + 2, RW = kTX + 2;
+    const size_t box_bytes = (size_t)RH * kROW * 4;
+    const size_t stage_bytes = box_bytes + (MASK ? (size_t)RH * kBW * 4 : 0);
+    auto stage_base = [&](int st) -> float* { return reinterpret_cast<float*>(smem_raw + (size_t)st * stage_bytes); };
+    auto stage_flags = [&](int st) -> uint32_t* {
+        return reinterpret_cast<uint32_t*>(smem_raw + (size_t)st * stage_bytes + box_bytes);
+    };
+    Sig* ring = reinterpret_cast<Sig*>(smem_raw + (size_t)P.nst * stage_bytes);
+    auto ring_at = [&](int slot, int ly, int lx) -> Sig& { return ring[(slot * RH + ly + 1) * RW + lx + 1]; };
+
+    const int t = threadIdx.x, tx = t & 31, ty = t >> 5;
+    const int cx = blockIdx.x % P.ncols, cy = blockIdx.x / P.ncols;
+    const int x0 = cx * kTX;
+    const int y0 = (int)(((long long)cy * g.ny) / P.R);
+    const int y1 = (int)(((long long)(cy + 1) * g.ny) / P.R);
+    const int TYt = y1 - y0;
+    const int z0 = blockIdx.y * P.zchunk;
+    const int z1 = min(z0 + P.zchunk, g.nz);
+    double dG_acc[kRedVals] = {0, 0, 0, 0, 0, 0};
+    if (z0 < z1) {
+        const int L = (z1 - z0) + 2;
+        const bool own_row = ty < TYt;
+        const int gx = wrap_any(x0 + tx, g.nx);
+        const int gy = own_row ? y0 + ty : y0;
+        const bool active = own_row && (x0 + tx < g.nx);
+        const int nh = 2 * RW + 2 * TYt;
+        const bool has_halo = t < nh;
+        int hlx = 0, hly = 0;
+        if (t < RW) { hlx = t - 1; hly = -1; }
+        else if (t < 2 * RW) { hlx = t - RW - 1; hly = TYt; }
+        else if (t < 2 * RW + TYt) { hlx = -1; hly = t - 2 * RW; }
+        else { hlx = kTX; hly = t - 2 * RW - TYt; }
+        const int hgx = wrap_any(x0 + hlx, g.nx), hgy = wrap_any(y0 + hly, g.ny);
+        auto plane_of = [&](int e) { return wrap_any(z0 - 1 + e, g.nz); };
+
+        // copier t (< RH * kCPR) owns chunk (jr, jc) of every box
+        const bool copier = t < RH * kCPR;
+        const int jr = t / kCPR, jc = t - (t / kCPR) * kCPR;
+        const int xs_chunk = wrap_any(x0 - 4 + jc * 4, g.nx);
+        // lambda box of population i: rows from y0 - 1 + c_iy (gather x + c_i)
+        const int yoff_m = wrap_any(y0 - 2 + jr, g.ny) * g.nx + xs_chunk;   // c_iy = -1
+        const int yoff_0 = wrap_any(y0 - 1 + jr, g.ny) * g.nx + xs_chunk;   // c_iy =  0 (and moments, flags)
+        const int yoff_p = wrap_any(y0 + jr, g.ny) * g.nx + xs_chunk;       // c_iy = +1
+        const int sdst = jr * kROW + jc * 4;
+        const int fdst = jr * kBW + jc * 4;
+
+        auto issue = [&](int e) {
+            if (e < L && copier) {
+                const int z = plane_of(e), st = e % P.nst;
+                const size_t pz_m = (size_t)wrap_dec(z, g.nz) * g.plane;   // c_iz = -1: plane z - 1
+                const size_t pz_0 = (size_t)z * g.plane;
+                const size_t pz_p = (size_t)wrap_inc(z, g.nz) * g.plane;   // c_iz = +1: plane z + 1
+                const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(stage_base(st) + sdst);
+                static_for<0, 2 * Q>([&](auto PP) {
+                    constexpr int pop = decltype(PP)::value;
+                    constexpr int i = pop % Q;
+                    const size_t pz = Vel<i>::z < 0 ? pz_m : (Vel<i>::z > 0 ? pz_p : pz_0);
+                    const int yo = Vel<i>::y < 0 ? yoff_m : (Vel<i>::y > 0 ? yoff_p : yoff_0);
+                    cp_async16(sbase + pop * kBW * 4, lam_in + (size_t)pop * g.N + pz + yo);
+                });
+                static_for<0, kMom>([&](auto CC) {
+                    constexpr int c = decltype(CC)::value;
+                    cp_async16(sbase + (2 * Q + c) * kBW * 4, mom + (size_t)c * g.N + pz_0 + yoff_0);
+                });
+                if constexpr (MASK)
+                    cp_async16((uint32_t)__cvta_generic_to_shared(stage_flags(st) + fdst), flags + pz_0 + yoff_0);
+            }
+            cp_commit();
+        };
+
+        // sigma of node (lx, ly); for own nodes also the local part of lambda_t
+        // (in mu) and the dL/dG term
+        auto node = [&](int st, int lx, int ly, int x, int y, int z, float (&mu)[2][Q], bool& solid,
+                        float& dG) -> Sig {
+            Sig sg = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+            dG = 0.f;
+            uint32_t fl = 0;
+            solid = false;
+            if constexpr (MASK) {
+                fl = stage_flags(st)[(ly + 1) * kBW + lx + 4];
+                solid = (fl & kSolid) != 0u;
+                if (solid) return sg;
+            }
+            const float* nb = stage_base(st) + (ly + 1) * kROW + lx + 4;
+            static_for<0, Q>([&](auto II) {
+                constexpr int i = decltype(II)::value;
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    if constexpr (MASK && i != 0) {
+                        if (fl & (1u << Vel<i>::opp)) {   // x + c_i solid: lambda_opp(i) at x
+                            const size_t own = (size_t)x + (size_t)g.nx * ((size_t)y + (size_t)g.ny * z);
+                            mu[k][i] = __ldg(lam_in + (size_t)(k * Q + Vel<i>::opp) * g.N + own);
+                            continue;
+                        }
+                    }
+                    mu[k][i] = nb[(k * Q + i) * kBW + Vel<i>::x];
+                }
+            });
+            float mo[kMom];
+#pragma unroll
+            for (int c = 0; c < kMom; ++c) mo[c] = nb[(2 * Q + c) * kBW];
+            float W[3], q[2];
+            adj_node(mo, mu, p, W, q, sg.a, sg.b, dG);
+            local_part(mu, p, W, q);
+            return sg;
+        };
+
+        for (int e = 0; e < P.nst; ++e) issue(e);
+        float cur[2][Q], nxt[2][Q];
+        bool solid_cur = true;
+        for (int e = 0; e < L; ++e) {
+            cp_wait_n(P.nst - 1);
+            __syncthreads();
+            const int st = e % P.nst, slot = e & 3;
+            const int z = plane_of(e);
+            bool solid_nxt = true;
+            if (own_row) {
+                float dG;
+                ring_at(slot, ty, tx) = node(st, tx, ty, gx, gy, z, nxt, solid_nxt, dG);
+                // dL/dG of the own nodes of the chunk's planes (not of the halo planes)
+                if (active && e >= 1 && e <= L - 2) dG_acc[0] += (double)dG;
+            }
+            if (has_halo) {
+                float dh[2][Q], dGh;
+                bool sh;
+                ring_at(slot, hly, hlx) = node(st, hlx, hly, hgx, hgy, z, dh, sh, dGh);
+            }
+            __syncthreads();
+            issue(e + P.nst);
+            if (e >= 2 && active) {
+                const int zc = plane_of(e - 1);
+                const size_t own = (size_t)gx + (size_t)g.nx * ((size_t)gy + (size_t)g.ny * zc);
+                float* out = lam_out + own;
+                if (solid_cur) {
+#pragma unroll
+                    for (int j = 0; j < 2 * Q; ++j) out[(size_t)j * g.N] = 0.f;
+                } else {
+                    // h^k = sum_{i>=1} w_i c_i . sigma^k(x - c_i); x - c_i lies in
+                    // plane (e - 1) - c_iz, i.e. ring slot e - 1 - c_iz
+                    float h[2] = {0.f, 0.f};
+                    static_for<1, Q>([&](auto II) {
+                        constexpr int i = decltype(II)::value;
+                        const int s2 = (e - 1 - Vel<i>::z) & 3;
+                        const Sig& sg = ring_at(s2, ty - Vel<i>::y, tx - Vel<i>::x);
+                        float acA = 0.f, acB = 0.f;
+                        if constexpr (Vel<i>::x != 0) { acA += Vel<i>::x * sg.a[0]; acB += Vel<i>::x * sg.b[0]; }
+                        if constexpr (Vel<i>::y != 0) { acA += Vel<i>::y * sg.a[1]; acB += Vel<i>::y * sg.b[1]; }
+                        if constexpr (Vel<i>::z != 0) { acA += Vel<i>::z * sg.a[2]; acB += Vel<i>::z * sg.b[2]; }
+                        h[0] += wgt<i>() * acA;
+                        h[1] += wgt<i>() * acB;
+                    });
+                    static_for<0, Q>([&](auto II) {
+                        constexpr int i = decltype(II)::value;
+#pragma unroll
+                        for (int k = 0; k < 2; ++k) __stcs(out + (size_t)(k * Q + i) * g.N, cur[k][i] + h[k]);
+                    });
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+#pragma unroll
+                for (int i = 0; i < Q; ++i) cur[k][i] = nxt[k][i];
+            solid_cur = solid_nxt;
+        }
+        cp_wait<0>();
+    }
+    block_sum_store(dG_acc, partials + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * kRedVals);
 }
 
 // lambda_T^k_i(x) = dL/drho^k(x) at fluid nodes.
@@ -259,21 +466,48 @@ __global__ void __launch_bounds__(256) adj_accumulate(const double* __restrict__
     if (threadIdx.x == 0) *acc += out[0];
 }
 
-template <typename S>
-cudaError_t pass_a(bool mask, const void* gt, const float* dpsi, const float* lam, const uint32_t* flags,
-                   float* aux, double* partials, const Geom& g, const Phys& p, cudaStream_t st) {
-    if (mask)
-        adj_pass_a<S, true><<<kRedBlocks, 256, 0, st>>>((const S*)gt, dpsi, lam, flags, aux, partials, g, p);
-    else
-        adj_pass_a<S, false><<<kRedBlocks, 256, 0, st>>>((const S*)gt, dpsi, lam, flags, aux, partials, g, p);
-    return cudaGetLastError();
-}
-
 }  // namespace
 
 size_t adjoint_workspace_bytes(int nx, int ny, int nz, int K) {
     const size_t N = (size_t)nx * ny * nz;
-    return 2 * a256(2 * Q * N * 4) + a256((size_t)kAux * N * 4) + a256((size_t)K * 2 * N * 4) + 256;
+    return 2 * a256(2 * Q * N * 4) + a256((size_t)kAux * N * 4) + a256((size_t)K * kMom * N * 4) + 256;
+}
+
+AsyncPlan plan_adjoint_box(int nx, int ny, int nz, int sm_count, bool masked, size_t smem_limit) {
+    AsyncPlan best{};
+    best.box = 0;
+    if (nx % 4 != 0) return best;   // 16-byte chunks of float rows
+    smem_limit = smem_limit > 4096 ? smem_limit - 4096 : 0;   // room for static shared memory
+    double best_cost = 1e300;
+    const int ncols = (nx + kTX - 1) / kTX;
+    for (int R = (ny + 15) / 16; R <= ny; ++R) {
+        const int tymax = (ny + R - 1) / R;
+        const int RH = tymax + 2;
+        const int threads = kTX * tymax;
+        if (threads < 2 * (kTX + 2) + 2 * tymax) continue;   // a thread per halo node
+        if (threads < RH * kCPR) continue;                     // a thread per chunk position
+        const size_t stage = (size_t)RH * kROW * 4 + (masked ? (size_t)RH * kBW * 4 : 0);
+        const size_t ring = (size_t)4 * RH * (kTX + 2) * sizeof(float) * 6;
+        if (smem_limit < ring + 2 * stage) continue;
+        int nst = (int)((smem_limit - ring) / stage);
+        nst = nst > 4 ? 4 : nst;
+        const long long bxy = (long long)ncols * R;
+        const int zs_max = nz / 4 > 1 ? nz / 4 : 1;
+        for (int zs = 1; zs <= zs_max; ++zs) {
+            const int zchunk = (nz + zs - 1) / zs;
+            const long long blocks = bxy * zs;
+            if (blocks > kRedBlocks) break;   // one partial row per block
+            const long long waves = (blocks + sm_count - 1) / sm_count;
+            const double work = (tymax + 0.6 * (2.0 * (kTX + 2) + 2.0 * tymax) / kTX) * (zchunk + 2);
+            const double cost = waves * work * (1.0 + 4.0 / tymax);
+            if (cost < best_cost * (1 - 1e-9)) {
+                best_cost = cost;
+                best = AsyncPlan{ncols, R, tymax, zs, zchunk, nst, threads, 0, ring + (size_t)nst * stage, 1};
+            }
+            if (blocks >= sm_count) break;
+        }
+    }
+    return best;
 }
 
 cudaError_t run_adjoint(const AdjointRun& R, const float* dLA, const float* dLB, float* gA, float* gB,
@@ -281,8 +515,22 @@ cudaError_t run_adjoint(const AdjointRun& R, const float* dLA, const float* dLB,
     const size_t N = (size_t)R.g.N;
     const unsigned nb = (unsigned)((N + 255) / 256);
     const bool mask = R.flags != nullptr;
+    const bool box = R.adjplan.box != 0;
     AdjBufs B = carve(R.adj, N, R.K);
     cudaError_t e;
+    if (box) {
+        // dynamic shared memory of this plan (the kernel also holds a small
+        // static FP64 reduction buffer, which the plan's limit leaves room for)
+        static size_t configured[2] = {0, 0};
+        if (configured[mask] < R.adjplan.smem) {
+            e = mask ? cudaFuncSetAttribute(adj_box_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)R.adjplan.smem)
+                     : cudaFuncSetAttribute(adj_box_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)R.adjplan.smem);
+            if (e != cudaSuccess) return e;
+            configured[mask] = R.adjplan.smem;
+        }
+    }
     adj_seed<<<nb, 256, 0, st>>>(dLA, dLB, R.flags, B.lam[0], R.g);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(B.gacc, 0, sizeof(double), st)) != cudaSuccess) return e;
@@ -298,36 +546,46 @@ cudaError_t run_adjoint(const AdjointRun& R, const float* dLA, const float* dLB,
     S.p = R.p;
     S.zsplit = R.zsplit;
     S.plan = R.plan;
+    const AsyncPlan& AP = R.adjplan;
+    const int adj_blocks = AP.ncols * AP.R * AP.zsplit;
     for (long long m = M - 1; m >= 0; --m) {
         const int Lm = (int)((T - m * R.K) < R.K ? (T - m * R.K) : R.K);
         if ((e = cudaMemcpyAsync(R.seg, R.ckpt + (size_t)m * R.state_bytes, R.state_bytes,
                                  cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
             return e;
-        // recompute the segment: states seg[0..Lm-1] and their density deviations
+        // recompute the segment: states seg[0..Lm-1] and their per-node moments
         for (int s = 0; s < Lm; ++s) {
             S.src = R.seg + (size_t)s * R.state_bytes;
             S.dst = (s + 1 < Lm) ? (void*)(R.seg + (size_t)(s + 1) * R.state_bytes) : R.scratch;
-            S.rho_out = B.segrho + (size_t)s * 2 * N;
+            S.mom_out = B.segmom + (size_t)s * kMom * N;
             if ((e = launch_step(S, st)) != cudaSuccess) return e;
         }
         // reverse through it
         for (int s = Lm - 1; s >= 0; --s) {
-            const void* gt = R.seg + (size_t)s * R.state_bytes;
-            const float* dpsi = B.segrho + (size_t)s * 2 * N;
-            switch (R.prec) {
-                case 0: e = pass_a<float>(mask, gt, dpsi, B.lam[cur], R.flags, B.aux, R.red_part, R.g, R.p, st); break;
-                case 1: e = pass_a<__half>(mask, gt, dpsi, B.lam[cur], R.flags, B.aux, R.red_part, R.g, R.p, st); break;
-                case 2:
-                    e = pass_a<__nv_bfloat16>(mask, gt, dpsi, B.lam[cur], R.flags, B.aux, R.red_part, R.g, R.p, st);
-                    break;
-                default: return cudaErrorInvalidValue;
+            const float* mom = B.segmom + (size_t)s * kMom * N;
+            if (box) {
+                dim3 grid(AP.ncols * AP.R, AP.zsplit, 1);
+                if (mask)
+                    adj_box_kernel<true><<<grid, AP.threads, AP.smem, st>>>(B.lam[cur], mom, R.flags, B.lam[1 - cur],
+                                                                           R.red_part, R.g, R.p, AP);
+                else
+                    adj_box_kernel<false><<<grid, AP.threads, AP.smem, st>>>(B.lam[cur], mom, R.flags,
+                                                                            B.lam[1 - cur], R.red_part, R.g, R.p, AP);
+                if ((e = cudaGetLastError()) != cudaSuccess) return e;
+                adj_accumulate<<<1, 256, 0, st>>>(R.red_part, adj_blocks, B.gacc);
+            } else {
+                if (mask)
+                    adj_pass_a<true><<<kRedBlocks, 256, 0, st>>>(mom, B.lam[cur], R.flags, B.aux, R.red_part, R.g, R.p);
+                else
+                    adj_pass_a<false><<<kRedBlocks, 256, 0, st>>>(mom, B.lam[cur], R.flags, B.aux, R.red_part, R.g,
+                                                                  R.p);
+                if ((e = cudaGetLastError()) != cudaSuccess) return e;
+                adj_accumulate<<<1, 256, 0, st>>>(R.red_part, kRedBlocks, B.gacc);
+                if (mask)
+                    adj_pass_b<true><<<nb, 256, 0, st>>>(B.lam[cur], B.aux, R.flags, B.lam[1 - cur], R.g, R.p);
+                else
+                    adj_pass_b<false><<<nb, 256, 0, st>>>(B.lam[cur], B.aux, R.flags, B.lam[1 - cur], R.g, R.p);
             }
-            if (e != cudaSuccess) return e;
-            adj_accumulate<<<1, 256, 0, st>>>(R.red_part, kRedBlocks, B.gacc);
-            if (mask)
-                adj_pass_b<true><<<nb, 256, 0, st>>>(B.lam[cur], B.aux, R.flags, B.lam[1 - cur], R.g, R.p);
-            else
-                adj_pass_b<false><<<nb, 256, 0, st>>>(B.lam[cur], B.aux, R.flags, B.lam[1 - cur], R.g, R.p);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             cur ^= 1;
         }

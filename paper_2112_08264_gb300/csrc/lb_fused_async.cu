@@ -146,7 +146,7 @@ __device__ __forceinline__ float2 consume_node(const AsyncPlan& P, const Smem& s
 template <typename S, bool MASK>
 __global__ void __launch_bounds__(kTX * kMaxTY, 1)
 fused_async_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t* __restrict__ flags,
-                   float* __restrict__ rho_out, Geom g, Phys p, AsyncPlan P) {
+                   float* __restrict__ mom_out, Geom g, Phys p, AsyncPlan P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem sm;
     sm.stage = reinterpret_cast<uint32_t*>(smem_raw);
@@ -212,11 +212,6 @@ fused_async_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_
             const int z = plane_of(e - 1);
             const long long own = gx + (long long)g.nx * (gy + (long long)g.ny * z);
             const int sm_m = (e - 2) & 3, sm_c = (e - 1) & 3, sm_p = e & 3;
-            if (rho_out != nullptr) {
-                const float2 r = ring_at(sm_c, ty, tx);
-                rho_out[own] = r.x;
-                rho_out[g.N + own] = r.y;
-            }
             if (!solid_cur) {
                 float dA, dB, j[3];
                 sums(cur, dA, dB, j);
@@ -227,6 +222,7 @@ fused_async_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_
                         return ring_at(s, ty + dy, tx + dx);
                     },
                     SA, SB);
+                if (mom_out != nullptr) store_moments(mom_out, g, own, dA, dB, j, SA, SB);
                 collide_store<S>(cur, p, dA, dB, j, SA, SB, dst, g, (int)own);
             }
         }
@@ -264,7 +260,7 @@ __device__ __forceinline__ void cp_async16(uint32_t saddr, const void* gptr) {
 template <typename S, bool MASK>
 __global__ void __launch_bounds__(kTX * kMaxTY, 1)
 fused_box_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t* __restrict__ flags,
-                 float* __restrict__ rho_out, Geom g, Phys p, AsyncPlan P) {
+                 float* __restrict__ mom_out, Geom g, Phys p, AsyncPlan P) {
     using B = BoxGeo<S>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int RH = P.tymax + 2, RW = kTX + 2;
@@ -397,11 +393,6 @@ fused_box_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t*
             const int zc = plane_of(e - 1);
             const long long own = gx + (long long)g.nx * (gy + (long long)g.ny * zc);
             const int sm_m = (e - 2) & 3, sm_c = (e - 1) & 3, sm_p = e & 3;
-            if (rho_out != nullptr) {
-                const float2 r = ring_at(sm_c, ty, tx);
-                rho_out[own] = r.x;
-                rho_out[g.N + own] = r.y;
-            }
             if (!solid_cur) {
                 float dA, dB, j[3];
                 sums(cur, dA, dB, j);
@@ -412,6 +403,7 @@ fused_box_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t*
                         return ring_at(s2, ty + dy, tx + dx);
                     },
                     SA, SB);
+                if (mom_out != nullptr) store_moments(mom_out, g, own, dA, dB, j, SA, SB);
                 collide_store<S>(cur, p, dA, dB, j, SA, SB, dst, g, (int)own);
             }
         }
@@ -428,14 +420,14 @@ template <typename S, bool MASK>
 cudaError_t launch_box_t(const StepLaunch& L, cudaStream_t st) {
     const AsyncPlan& P = L.plan;
     auto kern = fused_box_kernel<S, MASK>;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    static size_t configured = 0;
+    if (configured < P.smem) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem);
         if (e != cudaSuccess) return e;
-        configured = true;
+        configured = P.smem;
     }
     dim3 grid(P.ncols * P.R, P.zsplit, 1);
-    kern<<<grid, P.threads, P.smem, st>>>(static_cast<const S*>(L.src), static_cast<S*>(L.dst), L.flags, L.rho_out,
+    kern<<<grid, P.threads, P.smem, st>>>(static_cast<const S*>(L.src), static_cast<S*>(L.dst), L.flags, L.mom_out,
                                           L.g, L.p, P);
     return cudaGetLastError();
 }
@@ -444,14 +436,14 @@ template <typename S, bool MASK>
 cudaError_t launch_t(const StepLaunch& L, cudaStream_t st) {
     const AsyncPlan& P = L.plan;
     auto kern = fused_async_kernel<S, MASK>;
-    static bool configured = false;   // the attribute is per function, not per device state
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    static size_t configured = 0;   // the attribute is per function
+    if (configured < P.smem) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem);
         if (e != cudaSuccess) return e;
-        configured = true;
+        configured = P.smem;
     }
     dim3 grid(P.ncols * P.R, P.zsplit, 1);
-    kern<<<grid, P.threads, P.smem, st>>>(static_cast<const S*>(L.src), static_cast<S*>(L.dst), L.flags, L.rho_out,
+    kern<<<grid, P.threads, P.smem, st>>>(static_cast<const S*>(L.src), static_cast<S*>(L.dst), L.flags, L.mom_out,
                                           L.g, L.p, P);
     return cudaGetLastError();
 }

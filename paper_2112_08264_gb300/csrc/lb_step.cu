@@ -38,7 +38,7 @@ __device__ __forceinline__ int wrap_any(int a, int n) {
 template <typename S, bool MASK>
 __global__ void __launch_bounds__(kTX * kTY, 2)
 fused_step_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t* __restrict__ flags,
-                  float* __restrict__ rho_out, Geom g, Phys p, int zchunk) {
+                  float* __restrict__ mom_out, Geom g, Phys p, int zchunk) {
     __shared__ float2 ring[4][kTY + 2][kTX + 2];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * kTX + tx;
@@ -103,13 +103,6 @@ fused_step_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t
         }
         __syncthreads();
 
-        // optional density output (used by the adjoint's recompute)
-        if (rho_out != nullptr && active) {
-            const float2 r = ring[slot_c][ty + 1][tx + 1];
-            const long long own = gx + (long long)g.nx * (gy + (long long)g.ny * z);
-            rho_out[own] = r.x;
-            rho_out[g.N + own] = r.y;
-        }
         // collide plane z
         if (active && (!MASK || !(fl_cur & kSolid))) {
             float dA, dB, j[3];
@@ -121,7 +114,9 @@ fused_step_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t
                     return ring[s][ty + 1 + dy][tx + 1 + dx];
                 },
                 SA, SB);
-            collide_store<S>(cur, p, dA, dB, j, SA, SB, dst, g, gx + g.nx * (gy + g.ny * z));
+            const int own = gx + g.nx * (gy + g.ny * z);
+            if (mom_out != nullptr) store_moments(mom_out, g, own, dA, dB, j, SA, SB);
+            collide_store<S>(cur, p, dA, dB, j, SA, SB, dst, g, own);
         }
 #pragma unroll
         for (int k = 0; k < 2; ++k)
@@ -150,7 +145,7 @@ density_kernel(const S* __restrict__ src, const uint32_t* __restrict__ flags, fl
 template <typename S, bool MASK>
 __global__ void __launch_bounds__(256)
 collide_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t* __restrict__ flags,
-               const float* __restrict__ rho, Geom g, Phys p) {
+               const float* __restrict__ rho, float* __restrict__ mom_out, Geom g, Phys p) {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= g.N) return;
     const int x = (int)(s % g.nx);
@@ -177,6 +172,7 @@ collide_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t* _
             return make_float2(__ldg(rho + t), __ldg(rho + g.N + t));
         },
         SA, SB);
+    if (mom_out != nullptr) store_moments(mom_out, g, s, dA, dB, j, SA, SB);
     collide_store<S>(d, p, dA, dB, j, SA, SB, dst, g, (int)s);
 }
 
@@ -188,12 +184,11 @@ cudaError_t launch_step_t(const StepLaunch& L, cudaStream_t st) {
         dim3 block(kTX, kTY, 1);
         dim3 grid((L.g.nx + kTX - 1) / kTX, (L.g.ny + kTY - 1) / kTY, L.zsplit);
         const int zchunk = (L.g.nz + L.zsplit - 1) / L.zsplit;
-        fused_step_kernel<S, MASK><<<grid, block, 0, st>>>(src, dst, L.flags, L.rho_out, L.g, L.p, zchunk);
+        fused_step_kernel<S, MASK><<<grid, block, 0, st>>>(src, dst, L.flags, L.mom_out, L.g, L.p, zchunk);
     } else {
         const unsigned nb = (unsigned)((L.g.N + 255) / 256);
-        float* rho = L.rho_out != nullptr ? L.rho_out : L.rho;
-        density_kernel<S, MASK><<<nb, 256, 0, st>>>(src, L.flags, rho, L.g, L.p);
-        collide_kernel<S, MASK><<<nb, 256, 0, st>>>(src, dst, L.flags, rho, L.g, L.p);
+        density_kernel<S, MASK><<<nb, 256, 0, st>>>(src, L.flags, L.rho, L.g, L.p);
+        collide_kernel<S, MASK><<<nb, 256, 0, st>>>(src, dst, L.flags, L.rho, L.mom_out, L.g, L.p);
     }
     return cudaGetLastError();
 }
