@@ -228,7 +228,7 @@ adj_pass_b(const float* __restrict__ lam_in, const float* __restrict__ aux, cons
 constexpr int kBW = 40;               // box width (floats): 4 left of the tile, 32, 4 right
 constexpr int kCPR = kBW / 4;         // 16-byte chunks per box row
 constexpr int kBoxes = 2 * Q + kMom;  // lambda populations + moment fields
-constexpr int kROW = kBoxes * kBW;    // stage row stride (floats)
+constexpr int kROW = kBoxes * kBW + 4;   // stage row stride (floats), +16 bytes against bank conflicts
 
 __device__ __forceinline__ void cp_async16(uint32_t saddr, const void* gptr) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(gptr) : "memory");

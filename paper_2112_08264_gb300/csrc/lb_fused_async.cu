@@ -250,7 +250,9 @@ template <typename S> struct BoxGeo {
     static constexpr int PAD = CW;                   // box columns left of the tile
     static constexpr int BW = kTX + 2 * PAD;         // box width (elements)
     static constexpr int CPR = BW / CW;              // chunks per box row
-    static constexpr int ROW = 2 * Q * BW;           // stage row stride (elements)
+    // stage row stride (elements): the 38 boxes of a row plus 16 bytes so that
+    // vertically adjacent nodes (halo columns) fall in different banks
+    static constexpr int ROW = 2 * Q * BW + CW;
 };
 
 __device__ __forceinline__ void cp_async16(uint32_t saddr, const void* gptr) {
@@ -318,9 +320,9 @@ fused_box_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t*
         fdst = fr * 40 + fc * 4;
     }
 
-    auto issue = [&](int e) {
+    // copies of event e (plane z, stage st) into the stage
+    auto issue = [&](int e, int z, int st) {
         if (e < L) {
-            const int z = plane_of(e), st = e % P.nst;
             if (copier) {
                 // plane offsets for c_iz = -1, 0, +1 (source plane z - c_iz)
                 const size_t pz_m = (size_t)wrap_inc(z, g.nz) * g.plane;
@@ -371,47 +373,60 @@ fused_box_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t*
         return make_float2(dens_sum(d[0]), dens_sum(d[1]));
     };
 
-    for (int e = 0; e < P.nst; ++e) issue(e);
+    // planes and stages advance by one per event; tracked incrementally
+    const int zfirst = wrap_any(z0 - 1, g.nz);
+    {
+        int z = zfirst;
+        for (int e = 0; e < P.nst; ++e) {
+            issue(e, z, e);
+            z = wrap_inc(z, g.nz);
+        }
+    }
+    int z_cur = zfirst, z_prev = zfirst, st_cur = 0;
+    int z_iss = wrap_any(z0 - 1 + P.nst, g.nz);   // plane of event e + nst
+    const int own_off = (ty + 1) * RW + tx + 1;   // this node's ring cell within a slot
 
     float cur[2][Q], nxt[2][Q];
     bool solid_cur = true;
     for (int e = 0; e < L; ++e) {
         cp_wait_n(P.nst - 1);
         __syncthreads();   // every thread's chunks of event e are visible
-        const int st = e % P.nst, slot = e & 3;
-        const int z = plane_of(e);
+        const int slot = e & 3;
         bool solid_nxt = true;
-        if (own_row) ring_at(slot, ty, tx) = read_node(st, tx, ty, gx, gy, z, nxt, solid_nxt);
+        if (own_row) ring[slot * RH * RW + own_off] = read_node(st_cur, tx, ty, gx, gy, z_cur, nxt, solid_nxt);
         if (has_halo) {
             float dh[2][Q];
             bool sh;
-            ring_at(slot, hly, hlx) = read_node(st, hlx, hly, hgx, hgy, z, dh, sh);
+            ring_at(slot, hly, hlx) = read_node(st_cur, hlx, hly, hgx, hgy, z_cur, dh, sh);
         }
-        __syncthreads();   // ring of plane e complete; stage st fully read
-        issue(e + P.nst);
-        if (e >= 2 && active) {
-            const int zc = plane_of(e - 1);
-            const long long own = gx + (long long)g.nx * (gy + (long long)g.ny * zc);
-            const int sm_m = (e - 2) & 3, sm_c = (e - 1) & 3, sm_p = e & 3;
-            if (!solid_cur) {
-                float dA, dB, j[3];
-                sums(cur, dA, dB, j);
-                float SA[3], SB[3];
-                neighbour_sums(
-                    [&](int dx, int dy, int dz) {
-                        const int s2 = dz < 0 ? sm_m : (dz > 0 ? sm_p : sm_c);
-                        return ring_at(s2, ty + dy, tx + dx);
-                    },
-                    SA, SB);
-                if (mom_out != nullptr) store_moments(mom_out, g, own, dA, dB, j, SA, SB);
-                collide_store<S>(cur, p, dA, dB, j, SA, SB, dst, g, (int)own);
-            }
+        __syncthreads();   // ring of plane e complete; stage st_cur fully read
+        issue(e + P.nst, z_iss, st_cur);
+        if (e >= 2 && active && !solid_cur) {
+            const long long own = gx + (long long)g.nx * (gy + (long long)g.ny * z_prev);
+            const float2* rm = ring + ((e - 2) & 3) * RH * RW + own_off;
+            const float2* rc = ring + ((e - 1) & 3) * RH * RW + own_off;
+            const float2* rp = ring + slot * RH * RW + own_off;
+            float dA, dB, j[3];
+            sums(cur, dA, dB, j);
+            float SA[3], SB[3];
+            neighbour_sums(
+                [&](int dx, int dy, int dz) {
+                    const float2* r = dz < 0 ? rm : (dz > 0 ? rp : rc);
+                    return r[dy * RW + dx];
+                },
+                SA, SB);
+            if (mom_out != nullptr) store_moments(mom_out, g, own, dA, dB, j, SA, SB);
+            collide_store<S>(cur, p, dA, dB, j, SA, SB, dst, g, (int)own);
         }
 #pragma unroll
         for (int k = 0; k < 2; ++k)
 #pragma unroll
             for (int i = 0; i < Q; ++i) cur[k][i] = nxt[k][i];
         solid_cur = solid_nxt;
+        z_prev = z_cur;
+        z_cur = wrap_inc(z_cur, g.nz);
+        z_iss = wrap_inc(z_iss, g.nz);
+        st_cur = st_cur + 1 == P.nst ? 0 : st_cur + 1;
     }
     cp_wait<0>();
 }
@@ -483,7 +498,7 @@ AsyncPlan plan_fused_async(int nx, int ny, int nz, int sm_count, int prec, bool 
         const int ns = threads + 2 * (kTX + 2) + 2 * tymax;
         if (threads < 2 * (kTX + 2) + 2 * tymax) continue;   // every halo node needs a thread
         if (box && threads < (tymax + 2) * ((kTX + 2 * cw) / cw)) continue;   // a chunk per copier thread
-        const size_t stage = box ? (size_t)2 * Q * (tymax + 2) * (kTX + 2 * cw) * esize +
+        const size_t stage = box ? (size_t)(tymax + 2) * (2 * Q * (kTX + 2 * cw) + cw) * esize +
                                        (masked ? (size_t)(tymax + 2) * 40 * 4 : 0)
                                  : (size_t)2 * Q * ns * 4 + (masked ? (size_t)ns * 4 : 0) + (prec != 0 ? (size_t)ns * 8 : 0);
         const size_t ring = (size_t)4 * (tymax + 2) * (kTX + 2) * 8;
