@@ -391,6 +391,9 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_site": alg_bytes,
+                     "timed": ("the step kernel (one launch per step)" if info["launches_per_step"] == 1 else
+                               "the whole step (%d launches: step kernel(s) + write-side bounce-back)"
+                               % info["launches_per_step"]),
                      "traffic": (tps * N if tps is not None else None)},
         "gpu_launches": args.steps * info["launches_per_step"],
         "clocks": clocks,

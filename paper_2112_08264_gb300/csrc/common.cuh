@@ -33,9 +33,20 @@ struct Phys {
 // solid-site flags: bit 0 = this node is solid; bit i (1..18) = node x - c_i
 // is solid (so f_i(x) comes from bounce-back).
 constexpr uint32_t kSolid = 1u;
+// bits 1..Q-1: the pull source x - c_i of population i is solid
+constexpr uint32_t kNbSolidMask = ((1u << Q) - 1u) & ~1u;
 
 __device__ __forceinline__ int wrap_dec(int a, int n) { return a == 0 ? n - 1 : a - 1; }
 __device__ __forceinline__ int wrap_inc(int a, int n) { return a == n - 1 ? 0 : a + 1; }
+
+// Node x + c_i (periodic) of node (x, y, z), as a site index.
+template <int i>
+__device__ __forceinline__ long long nb_index(const Geom& g, int x, int y, int z) {
+    const int xx = Vel<i>::x > 0 ? wrap_inc(x, g.nx) : (Vel<i>::x < 0 ? wrap_dec(x, g.nx) : x);
+    const int yy = Vel<i>::y > 0 ? wrap_inc(y, g.ny) : (Vel<i>::y < 0 ? wrap_dec(y, g.ny) : y);
+    const int zz = Vel<i>::z > 0 ? wrap_inc(z, g.nz) : (Vel<i>::z < 0 ? wrap_dec(z, g.nz) : z);
+    return xx + (long long)g.nx * (yy + (long long)g.ny * zz);
+}
 
 // Site indices of the pull sources x - c_i for the 19 velocities.
 struct PullIdx {
@@ -86,9 +97,7 @@ __device__ __forceinline__ float dens_sum(const float (&d)[Q]) {
 // j = sum_k sum_i c_i d_i^k (sum_i c_i w_i rho0 = 0, so the deviations carry
 // the whole momentum). The momentum is summed over opposite pairs,
 // c_i (d_i - d_opp(i)), whose differences are exact when the two are close.
-__device__ __forceinline__ void sums(const float (&d)[2][Q], float& dA, float& dB, float (&j)[3]) {
-    dA = dens_sum(d[0]);
-    dB = dens_sum(d[1]);
+__device__ __forceinline__ void momentum(const float (&d)[2][Q], float (&j)[3]) {
     j[0] = j[1] = j[2] = 0.f;
     static_for<0, 9>([&](auto M) {
         constexpr int i = 2 * decltype(M)::value + 1;   // (i, i + 1) are opposite
@@ -99,6 +108,12 @@ __device__ __forceinline__ void sums(const float (&d)[2][Q], float& dA, float& d
     });
 }
 
+__device__ __forceinline__ void sums(const float (&d)[2][Q], float& dA, float& dB, float (&j)[3]) {
+    dA = dens_sum(d[0]);
+    dB = dens_sum(d[1]);
+    momentum(d, j);
+}
+
 // BGK collision with the Shan-Chen velocity shift, in deviation form, and
 // store of the post-collision node.
 //   SA, SB: sum_{i>=1} w_i psi^k(x + c_i) c_i for k = A, B.
@@ -107,11 +122,13 @@ __device__ __forceinline__ void sums(const float (&d)[2][Q], float& dA, float& d
 // Equilibrium deviation: f^eq_i - w_i rho0 = w_i [(rho - rho0) + rho (3 c.u
 // + 4.5 (c.u)^2 - 1.5 u.u)] (Eq. LEQ with c_s^2 = 1/3); the stored value is
 // (1 - omega) d_i + omega (f^eq_i - w_i rho0).
-template <typename S>
+// With Z, a lane with zero set stores 0 in every slot (a solid node).
+template <typename S, bool Z = false>
 __device__ __forceinline__ void collide_store(const float (&d)[2][Q], const Phys& p, float dA, float dB,
                                               const float (&j)[3], const float (&SA)[3],
                                               const float (&SB)[3], S* __restrict__ dst,
-                                              const Geom& g, int own) {
+                                              const Geom& g, int own, bool zero = false) {
+    auto put = [&](S* a, float v) { Store<S>::st(a, (Z && zero) ? 0.f : v); };
     const float rA = p.rho0[0] + dA, rB = p.rho0[1] + dB;
     const float inv = 1.0f / (rA + rB);
     const float up[3] = {j[0] * inv, j[1] * inv, j[2] * inv};
@@ -133,7 +150,7 @@ __device__ __forceinline__ void collide_store(const float (&d)[2][Q], const Phys
         S* out = dst + (size_t)(k * Q) * (size_t)g.N + (size_t)own;
         {
             const float eq0 = p.omega * (1.0f / 3.0f) * (drk - rk * uu15);
-            Store<S>::st(out, om1 * d[k][0] + eq0);
+            put(out, om1 * d[k][0] + eq0);
         }
         static_for<0, 9>([&](auto M) {
             constexpr int i = 2 * decltype(M)::value + 1;   // (i, i + 1) opposite
@@ -145,8 +162,8 @@ __device__ __forceinline__ void collide_store(const float (&d)[2][Q], const Phys
             const float wr = axis ? wr1 : wr2, wd = axis ? wd1 : wd2;
             const float even = wr * (4.5f * cu * cu - uu15) + wd;
             const float odd = 3.0f * wr * cu;
-            Store<S>::st(out + (size_t)i * g.N, om1 * d[k][i] + (even + odd));
-            Store<S>::st(out + (size_t)(i + 1) * g.N, om1 * d[k][i + 1] + (even - odd));
+            put(out + (size_t)i * g.N, om1 * d[k][i] + (even + odd));
+            put(out + (size_t)(i + 1) * g.N, om1 * d[k][i + 1] + (even - odd));
         });
     }
 }

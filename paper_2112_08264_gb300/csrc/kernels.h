@@ -50,10 +50,16 @@ cudaError_t launch_fused_async(const StepLaunch& L, cudaStream_t st);
 // Solid flags from a device mask (1 = solid).
 cudaError_t launch_flags(const uint8_t* mask, uint32_t* flags, const Geom& g, cudaStream_t st);
 
+// Write-side halfway bounce-back on a freshly written state g: for every fluid
+// node x and direction i with x + c_i solid, copy g_i(x) into slot opp(i) of
+// x + c_i. The next pull of population opp(i) at x, from x - c_opp(i) = x + c_i,
+// then reads the bounced value without a mask test. Run after every masked step.
+cudaError_t launch_reflect(int prec, void* g_state, const uint32_t* flags, const Geom& g, cudaStream_t st);
+
 // Internal state from a post-streaming population field: either the
 // equilibrium of (rhoA, rhoB, u) (f == nullptr) or the given f (float,
 // [k][i][s]). Inverse of the pull: g_j(y) = f_j(y + c_j) if y + c_j is fluid,
-// else f_opp(j)(y).
+// else f_opp(j)(y); solid slots are filled as launch_reflect fills them.
 cudaError_t launch_unstream(int prec, void* dst, const uint32_t* flags, const float* f,
                             const float* rhoA, const float* rhoB, const float* u, const Geom& g,
                             const Phys& p, cudaStream_t st);

@@ -359,7 +359,8 @@ lb_status lb_backward(lb_ctx* c, const float* dLA, const float* dLB, float* gA, 
 lb_status lb_launch_info(const lb_ctx* c, int* launches, int* blocks, int* threads, int* zsplit) {
     if (!c) return LB_EINVAL;
     const int k = c->opt.kernel;
-    if (launches) *launches = k == LB_KERNEL_TWO_PASS ? 2 : 1;
+    // a masked step adds the write-side bounce-back pass (launch_reflect)
+    if (launches) *launches = (k == LB_KERNEL_TWO_PASS ? 2 : 1) + (c->has_mask ? 1 : 0);
     if (blocks)
         *blocks = k == LB_KERNEL_FUSED ? c->plan.ncols * c->plan.R * c->plan.zsplit
                 : k == LB_KERNEL_FUSED_REG ? c->tiles * c->zsplit : (int)((c->g.N + 255) / 256);

@@ -32,8 +32,43 @@ __global__ void flags_kernel(const uint8_t* __restrict__ mask, uint32_t* __restr
     flags[s] = f;
 }
 
+// One thread per node. The read slots (population i at fluid x) and the
+// written slots (population opp(i) at solid x + c_i) are disjoint, so the
+// read and write views are restrict-qualified and every load of a node is in
+// flight before its first store.
+template <typename S>
+__global__ void reflect_kernel(const S* __restrict__ in, S* __restrict__ out,
+                               const uint32_t* __restrict__ flags, Geom g) {
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.N) return;
+    const uint32_t fl = __ldg(flags + s);
+    if ((fl & kSolid) || !(fl & kNbSolidMask)) return;
+    int x, y, z;
+    site_xyz(s, g, x, y, z);
+    S v[2][Q];
+    static_for<1, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        if (fl & (1u << Vel<i>::opp)) {   // x - c_opp(i) = x + c_i is solid
+#pragma unroll
+            for (int k = 0; k < 2; ++k) v[k][i] = in[(size_t)(k * Q + i) * g.N + s];
+        }
+    });
+    static_for<1, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int o = Vel<i>::opp;
+        if (fl & (1u << o)) {
+            const long long t = nb_index<i>(g, x, y, z);
+#pragma unroll
+            for (int k = 0; k < 2; ++k) out[(size_t)(k * Q + o) * g.N + t] = v[k][i];
+        }
+    });
+}
+
 // g_j(y) = f_j(y + c_j) if y + c_j is fluid, else f_opp(j)(y); f is either the
-// given field or the equilibrium of (rho^k, u).
+// given field or the equilibrium of (rho^k, u). Solid nodes y get the same
+// streaming source g_j(y) = f_j(y + c_j) where y + c_j is fluid (0 elsewhere):
+// the fluid node x = y + c_j, whose population j bounces back at y, may read
+// it there instead of g_opp(j)(x), which holds the same value.
 template <typename S, bool FROM_F>
 __global__ void unstream_kernel(S* __restrict__ dst, const uint32_t* __restrict__ flags,
                                 const float* __restrict__ f, const float* __restrict__ rhoA,
@@ -44,17 +79,20 @@ __global__ void unstream_kernel(S* __restrict__ dst, const uint32_t* __restrict_
     int x, y, z;
     site_xyz(s, g, x, y, z);
     const uint32_t fl = flags ? flags[s] : 0u;
-    if (fl & kSolid) {
-        for (int j = 0; j < 2 * Q; ++j) Store<S>::st(dst + (size_t)j * g.N + s, 0.f);
-        return;
-    }
+    const bool solid = (fl & kSolid) != 0u;
     const int xm = wrap_dec(x, g.nx), xp = wrap_inc(x, g.nx);
     const int ym = wrap_dec(y, g.ny), yp = wrap_inc(y, g.ny);
     const int zm = wrap_dec(z, g.nz), zp = wrap_inc(z, g.nz);
     static_for<0, Q>([&](auto J) {
         constexpr int j = decltype(J)::value;
         // destination neighbour y + c_j is solid <=> flag bit opp(j) (y - c_opp(j))
-        const bool back = (j != 0) && (fl & (1u << Vel<j>::opp));
+        const bool nb_solid = (j != 0) && (fl & (1u << Vel<j>::opp));
+        const bool back = nb_solid && !solid;
+        if (solid && (j == 0 || nb_solid)) {   // not read by any fluid node
+#pragma unroll
+            for (int k = 0; k < 2; ++k) Store<S>::st(dst + (size_t)(k * Q + j) * g.N + s, 0.f);
+            return;
+        }
         const int tx = Vel<j>::x == 1 ? xp : (Vel<j>::x == -1 ? xm : x);
         const int ty = Vel<j>::y == 1 ? yp : (Vel<j>::y == -1 ? ym : y);
         const int tz = Vel<j>::z == 1 ? zp : (Vel<j>::z == -1 ? zm : z);
@@ -243,6 +281,13 @@ cudaError_t by_prec(int prec, F4&& f32, F3&& f16, F2&& bf16) {
 cudaError_t launch_flags(const uint8_t* mask, uint32_t* flags, const Geom& g, cudaStream_t st) {
     flags_kernel<<<blocks_for(g.N, 256), 256, 0, st>>>(mask, flags, g);
     return cudaGetLastError();
+}
+
+cudaError_t launch_reflect(int prec, void* g_state, const uint32_t* flags, const Geom& g, cudaStream_t st) {
+    const unsigned nb = blocks_for(g.N, 256);
+#define LBGB_REFLECT(T) [&] { reflect_kernel<T><<<nb, 256, 0, st>>>((const T*)g_state, (T*)g_state, flags, g); }
+    return by_prec(prec, LBGB_REFLECT(float), LBGB_REFLECT(__half), LBGB_REFLECT(__nv_bfloat16));
+#undef LBGB_REFLECT
 }
 
 cudaError_t launch_unstream(int prec, void* dst, const uint32_t* flags, const float* f, const float* rhoA,

@@ -290,13 +290,15 @@ fused_box_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t*
     const int gx = wrap_any(x0 + tx, g.nx);
     const int gy = own_row ? y0 + ty : y0;
     const bool active = own_row && (x0 + tx < g.nx);
+    // halo nodes go to the last threads (the first ones issue the copies)
     const int nh = 2 * RW + 2 * TYt;
-    const bool has_halo = t < nh;
+    const int h = t - (P.threads - nh);
+    const bool has_halo = h >= 0;
     int hlx = 0, hly = 0;
-    if (t < RW) { hlx = t - 1; hly = -1; }
-    else if (t < 2 * RW) { hlx = t - RW - 1; hly = TYt; }
-    else if (t < 2 * RW + TYt) { hlx = -1; hly = t - 2 * RW; }
-    else { hlx = kTX; hly = t - 2 * RW - TYt; }
+    if (h < RW) { hlx = h - 1; hly = -1; }
+    else if (h < 2 * RW) { hlx = h - RW - 1; hly = TYt; }
+    else if (h < 2 * RW + TYt) { hlx = -1; hly = h - 2 * RW; }
+    else { hlx = kTX; hly = h - 2 * RW - TYt; }
     const int hgx = wrap_any(x0 + hlx, g.nx), hgy = wrap_any(y0 + hly, g.ny);
 
     auto plane_of = [&](int e) { return wrap_any(z0 - 1 + e, g.nz); };
@@ -346,30 +348,19 @@ fused_box_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t*
         cp_commit();
     };
 
-    // pulled deviations of node (lx, ly) at plane z from stage st
-    auto read_node = [&](int st, int lx, int ly, int x, int y, int z, float (&d)[2][Q], bool& solid) -> float2 {
-        uint32_t fl = 0;
-        solid = false;
-        if constexpr (MASK) {
-            fl = stage_flags(st)[(ly + 1) * 40 + lx + 4];
-            solid = (fl & kSolid) != 0u;
-            if (solid) return make_float2(-p.rho0[0], -p.rho0[1]);
-        }
+    // pulled deviations of node (lx, ly) from stage st. A population whose
+    // source node is solid was stored in that solid node's slot by the
+    // write-side bounce-back, so every pull is the same box read.
+    // (solid lanes read finite placeholders and report psi = 0)
+    auto read_node = [&](int st, int lx, int ly, float (&d)[2][Q], uint32_t& fl) -> float2 {
+        fl = MASK ? stage_flags(st)[(ly + 1) * 40 + lx + 4] : 0u;
         const S* nb = stage_base(st) + (ly + 1) * B::ROW + lx + B::PAD;
         static_for<0, Q>([&](auto II) {
             constexpr int i = decltype(II)::value;
 #pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                if constexpr (MASK && i != 0) {
-                    if (fl & (1u << i)) {   // bounce-back: own node, opposite population
-                        const size_t own = (size_t)x + (size_t)g.nx * ((size_t)y + (size_t)g.ny * z);
-                        d[k][i] = Store<S>::ld(src + (size_t)(k * Q + Vel<i>::opp) * g.N + own);
-                        continue;
-                    }
-                }
-                d[k][i] = Store<S>::to_f(nb[(k * Q + i) * B::BW - Vel<i>::x]);
-            }
+            for (int k = 0; k < 2; ++k) d[k][i] = Store<S>::to_f(nb[(k * Q + i) * B::BW - Vel<i>::x]);
         });
+        if (MASK && (fl & kSolid)) return make_float2(-p.rho0[0], -p.rho0[1]);
         return make_float2(dens_sum(d[0]), dens_sum(d[1]));
     };
 
@@ -387,27 +378,38 @@ fused_box_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t*
     const int own_off = (ty + 1) * RW + tx + 1;   // this node's ring cell within a slot
 
     float cur[2][Q], nxt[2][Q];
-    bool solid_cur = true;
+    uint32_t fl_cur = kSolid;
     for (int e = 0; e < L; ++e) {
         cp_wait_n(P.nst - 1);
         __syncthreads();   // every thread's chunks of event e are visible
         const int slot = e & 3;
-        bool solid_nxt = true;
-        if (own_row) ring[slot * RH * RW + own_off] = read_node(st_cur, tx, ty, gx, gy, z_cur, nxt, solid_nxt);
+        uint32_t fl_nxt = kSolid;
+        if (own_row) ring[slot * RH * RW + own_off] = read_node(st_cur, tx, ty, nxt, fl_nxt);
         if (has_halo) {
             float dh[2][Q];
-            bool sh;
-            ring_at(slot, hly, hlx) = read_node(st_cur, hlx, hly, hgx, hgy, z_cur, dh, sh);
+            uint32_t fh;
+            ring_at(slot, hly, hlx) = read_node(st_cur, hlx, hly, dh, fh);
         }
         __syncthreads();   // ring of plane e complete; stage st_cur fully read
         issue(e + P.nst, z_iss, st_cur);
-        if (e >= 2 && active && !solid_cur) {
+        // Solid lanes run the same code and store zeros, so that every warp
+        // stores whole sectors (a partly written sector costs a DRAM read);
+        // the solid slots a fluid node pulls are filled afterwards by the
+        // bounce-back pass. (The fl_cur test on unmasked FP32 grids is always
+        // true; it is kept because that form schedules measurably faster.)
+        if (e >= 2 && active && (MASK || sizeof(S) != 4 || !(fl_cur & kSolid))) {
             const long long own = gx + (long long)g.nx * (gy + (long long)g.ny * z_prev);
             const float2* rm = ring + ((e - 2) & 3) * RH * RW + own_off;
             const float2* rc = ring + ((e - 1) & 3) * RH * RW + own_off;
             const float2* rp = ring + slot * RH * RW + own_off;
             float dA, dB, j[3];
-            sums(cur, dA, dB, j);
+            if constexpr (sizeof(S) == 4) {
+                sums(cur, dA, dB, j);
+            } else {   // own density deviations are already in the ring (same sums)
+                dA = rc[0].x;
+                dB = rc[0].y;
+                momentum(cur, j);
+            }
             float SA[3], SB[3];
             neighbour_sums(
                 [&](int dx, int dy, int dz) {
@@ -415,14 +417,15 @@ fused_box_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t*
                     return r[dy * RW + dx];
                 },
                 SA, SB);
-            if (mom_out != nullptr) store_moments(mom_out, g, own, dA, dB, j, SA, SB);
-            collide_store<S>(cur, p, dA, dB, j, SA, SB, dst, g, (int)own);
+            const bool solid = MASK && (fl_cur & kSolid);
+            if (mom_out != nullptr && !solid) store_moments(mom_out, g, own, dA, dB, j, SA, SB);
+            collide_store<S, MASK>(cur, p, dA, dB, j, SA, SB, dst, g, (int)own, solid);
         }
 #pragma unroll
         for (int k = 0; k < 2; ++k)
 #pragma unroll
             for (int i = 0; i < Q; ++i) cur[k][i] = nxt[k][i];
-        solid_cur = solid_nxt;
+        fl_cur = fl_nxt;
         z_prev = z_cur;
         z_cur = wrap_inc(z_cur, g.nz);
         z_iss = wrap_inc(z_iss, g.nz);

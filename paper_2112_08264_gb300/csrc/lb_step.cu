@@ -195,7 +195,8 @@ cudaError_t launch_step_t(const StepLaunch& L, cudaStream_t st) {
 
 }  // namespace
 
-cudaError_t launch_step(const StepLaunch& L, cudaStream_t st) {
+namespace {
+cudaError_t launch_step_kernels(const StepLaunch& L, cudaStream_t st) {
     if (L.kernel == 0) return launch_fused_async(L, st);
     const bool m = L.flags != nullptr;
     switch (L.prec) {
@@ -205,6 +206,13 @@ cudaError_t launch_step(const StepLaunch& L, cudaStream_t st) {
             return m ? launch_step_t<__nv_bfloat16, true>(L, st) : launch_step_t<__nv_bfloat16, false>(L, st);
         default: return cudaErrorInvalidValue;
     }
+}
+}  // namespace
+
+cudaError_t launch_step(const StepLaunch& L, cudaStream_t st) {
+    const cudaError_t e = launch_step_kernels(L, st);
+    if (e != cudaSuccess || L.flags == nullptr) return e;
+    return launch_reflect(L.prec, L.dst, L.flags, L.g, st);
 }
 
 void fused_geometry(int nx, int ny, int nz, int sm_count, int* tiles, int* zsplit, int* threads) {
