@@ -2,7 +2,8 @@
 // reduction kernels.
 //
 // State in device memory: the POST-COLLISION populations g of the last step,
-// stored as deviations d = g - w_i rho0^k, [k][i][s]. One step is then a pull
+// stored as deviations d = g - w_i rho0^k in blocked SoA order (pidx below).
+// One step is then a pull
 // (Sec. 3 one-step two-grid scheme, two buffers, read one / write the other):
 //   f_i(x) = g_i(x - c_i)         if x - c_i is fluid   (streaming, Eq. bgk)
 //   f_i(x) = g_opp(i)(x)          if x - c_i is solid   (halfway bounce-back at
@@ -19,8 +20,28 @@ namespace lbgb {
 struct Geom {
     int nx, ny, nz;
     int plane;       // nx * ny
-    long long N;     // sites; population (k, i) starts at (k * 19 + i) * N
+    long long N;     // sites, s = x + nx (y + ny z)
 };
+
+// Blocked SoA storage of the 2Q populations q = k Q + i: the site index s is
+// cut into blocks of kBlk consecutive sites; a block holds population 0 of
+// its sites, then population 1, ..., each as kBlk contiguous values. A warp's
+// access to one population of 32 consecutive sites is one contiguous
+// segment, as in plain SoA, while the offset of population q within a block
+// is the constant q * kBlk, so that the 38 accesses of a node share one
+// address and differ by immediates.
+// Site indices are below 2^31 (checked at context creation), so the split
+// is an unsigned 32-bit shift and mask.
+constexpr int kBlk = 64;
+static_assert((kBlk & (kBlk - 1)) == 0, "kBlk must be a power of two");
+__host__ __device__ __forceinline__ size_t blk_base(uint32_t s) {
+    return (size_t)(s / (uint32_t)kBlk) * (size_t)(2 * Q * kBlk) + (size_t)(s % (uint32_t)kBlk);
+}
+__host__ __device__ __forceinline__ size_t pidx(int q, uint32_t s) { return blk_base(s) + (size_t)q * kBlk; }
+// elements of one state (the last block is padded)
+__host__ __device__ __forceinline__ size_t state_elems(long long N) {
+    return (size_t)((N + kBlk - 1) / kBlk) * (size_t)(2 * Q * kBlk);
+}
 
 struct Phys {
     float tau;       // relaxation time
@@ -82,7 +103,7 @@ __device__ __forceinline__ void pull(const S* __restrict__ src, const Geom& g, c
         }
 #pragma unroll
         for (int k = 0; k < 2; ++k)
-            d[k][i] = Store<S>::ld(src + (size_t)(k * Q + pop) * (size_t)g.N + (size_t)idx);
+            d[k][i] = Store<S>::ld(src + pidx(k * Q + pop, idx));
     });
 }
 
@@ -147,7 +168,7 @@ __device__ __forceinline__ void collide_store(const float (&d)[2][Q], const Phys
         // odd in c (3 w rho c.u)
         const float wr1 = p.omega * (1.0f / 18.0f) * rk, wd1 = p.omega * (1.0f / 18.0f) * drk;
         const float wr2 = p.omega * (1.0f / 36.0f) * rk, wd2 = p.omega * (1.0f / 36.0f) * drk;
-        S* out = dst + (size_t)(k * Q) * (size_t)g.N + (size_t)own;
+        S* out = dst + blk_base(own) + k * Q * kBlk;
         {
             const float eq0 = p.omega * (1.0f / 3.0f) * (drk - rk * uu15);
             put(out, om1 * d[k][0] + eq0);
@@ -162,8 +183,8 @@ __device__ __forceinline__ void collide_store(const float (&d)[2][Q], const Phys
             const float wr = axis ? wr1 : wr2, wd = axis ? wd1 : wd2;
             const float even = wr * (4.5f * cu * cu - uu15) + wd;
             const float odd = 3.0f * wr * cu;
-            put(out + (size_t)i * g.N, om1 * d[k][i] + (even + odd));
-            put(out + (size_t)(i + 1) * g.N, om1 * d[k][i + 1] + (even - odd));
+            put(out + i * kBlk, om1 * d[k][i] + (even + odd));
+            put(out + (i + 1) * kBlk, om1 * d[k][i + 1] + (even - odd));
         });
     }
 }

@@ -65,7 +65,7 @@ bool valid_options(const lb_options& o) {
 Layout make_layout(int nx, int ny, int nz, const lb_options& o) {
     Layout L{};
     const size_t N = (size_t)nx * ny * nz;
-    L.state_bytes = align256(2 * Q * N * store_bytes(o.prec));
+    L.state_bytes = align256(state_elems((long long)N) * store_bytes(o.prec));
     size_t off = 0;
     L.pop[0] = off; off += L.state_bytes;
     L.pop[1] = off; off += L.state_bytes;

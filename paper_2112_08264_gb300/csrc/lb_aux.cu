@@ -50,7 +50,7 @@ __global__ void reflect_kernel(const S* __restrict__ in, S* __restrict__ out,
         constexpr int i = decltype(I)::value;
         if (fl & (1u << Vel<i>::opp)) {   // x - c_opp(i) = x + c_i is solid
 #pragma unroll
-            for (int k = 0; k < 2; ++k) v[k][i] = in[(size_t)(k * Q + i) * g.N + s];
+            for (int k = 0; k < 2; ++k) v[k][i] = in[pidx(k * Q + i, s)];
         }
     });
     static_for<1, Q>([&](auto I) {
@@ -59,7 +59,7 @@ __global__ void reflect_kernel(const S* __restrict__ in, S* __restrict__ out,
         if (fl & (1u << o)) {
             const long long t = nb_index<i>(g, x, y, z);
 #pragma unroll
-            for (int k = 0; k < 2; ++k) out[(size_t)(k * Q + o) * g.N + t] = v[k][i];
+            for (int k = 0; k < 2; ++k) out[pidx(k * Q + o, t)] = v[k][i];
         }
     });
 }
@@ -90,7 +90,7 @@ __global__ void unstream_kernel(S* __restrict__ dst, const uint32_t* __restrict_
         const bool back = nb_solid && !solid;
         if (solid && (j == 0 || nb_solid)) {   // not read by any fluid node
 #pragma unroll
-            for (int k = 0; k < 2; ++k) Store<S>::st(dst + (size_t)(k * Q + j) * g.N + s, 0.f);
+            for (int k = 0; k < 2; ++k) Store<S>::st(dst + pidx(k * Q + j, s), 0.f);
             return;
         }
         const int tx = Vel<j>::x == 1 ? xp : (Vel<j>::x == -1 ? xm : x);
@@ -114,7 +114,7 @@ __global__ void unstream_kernel(S* __restrict__ dst, const uint32_t* __restrict_
                 }
                 dev = wgt<j>() * ((r - p.rho0[k]) + r * (cu * (3.0f + 4.5f * cu) - 1.5f * uu));
             }
-            Store<S>::st(dst + (size_t)(k * Q + j) * g.N + s, dev);
+            Store<S>::st(dst + pidx(k * Q + j, s), dev);
         }
     });
 }

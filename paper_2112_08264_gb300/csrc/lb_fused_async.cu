@@ -114,7 +114,7 @@ __device__ __forceinline__ void issue_node(const S* __restrict__ src, const uint
         }
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
-            const S* ep = src + (size_t)(k * Q + pop) * (size_t)g.N + (size_t)idx;
+            const S* ep = src + pidx(k * Q + pop, idx);
             cp_async4((uint32_t)__cvta_generic_to_shared(base + (size_t)(k * Q + i) * P.ns), Word<S>::addr(ep));
             hb |= (unsigned long long)Word<S>::half(ep) << (k * Q + i);
         }
@@ -336,7 +336,8 @@ fused_box_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t*
                     constexpr int i = pop % Q;
                     const size_t pz = Vel<i>::z < 0 ? pz_m : (Vel<i>::z > 0 ? pz_p : pz_0);
                     const int yo = Vel<i>::y < 0 ? yoff_m : (Vel<i>::y > 0 ? yoff_p : yoff_0);
-                    cp_async16(sbase + pop * B::BW * (int)sizeof(S), src + (size_t)pop * g.N + pz + yo);
+                    // a chunk starts at a multiple of CW and so lies inside one block
+                    cp_async16(sbase + pop * B::BW * (int)sizeof(S), src + blk_base((uint32_t)(pz + yo)) + pop * kBlk);
                 });
             }
             if constexpr (MASK) {
