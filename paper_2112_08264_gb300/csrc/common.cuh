@@ -23,21 +23,24 @@ struct Geom {
     long long N;     // sites, s = x + nx (y + ny z)
 };
 
-// Blocked SoA storage of the 2Q populations q = k Q + i: the site index s is
-// cut into blocks of kBlk consecutive sites; a block holds population 0 of
-// its sites, then population 1, ..., each as kBlk contiguous values. A warp's
-// access to one population of 32 consecutive sites is one contiguous
-// segment, as in plain SoA, while the offset of population q within a block
-// is the constant q * kBlk, so that the 38 accesses of a node share one
-// address and differ by immediates.
-// Site indices are below 2^31 (checked at context creation), so the split
-// is an unsigned 32-bit shift and mask.
+// Blocked SoA storage: the site index s is cut into blocks of kBlk
+// consecutive sites; a block holds velocity 0 of its sites, then velocity 1,
+// ..., each as kBlk (A, B) component pairs, so that
+//   element(k, i, s) = block(s) + i * 2 kBlk + 2 (s mod kBlk) + k.
+// A warp's access to one velocity of 32 consecutive sites is one contiguous
+// segment, both components of a velocity move as one vector access (they
+// stream along the same c_i), and the offset of velocity i within a block is
+// the constant i * 2 kBlk, so the 19 accesses of a node share one address
+// and differ by immediates. Site indices are below 2^31 (checked at context
+// creation): the split is an unsigned 32-bit shift and mask.
 constexpr int kBlk = 64;
 static_assert((kBlk & (kBlk - 1)) == 0, "kBlk must be a power of two");
 __host__ __device__ __forceinline__ size_t blk_base(uint32_t s) {
-    return (size_t)(s / (uint32_t)kBlk) * (size_t)(2 * Q * kBlk) + (size_t)(s % (uint32_t)kBlk);
+    return (size_t)(s / (uint32_t)kBlk) * (size_t)(2 * Q * kBlk) + 2 * (size_t)(s % (uint32_t)kBlk);
 }
-__host__ __device__ __forceinline__ size_t pidx(int q, uint32_t s) { return blk_base(s) + (size_t)q * kBlk; }
+__host__ __device__ __forceinline__ size_t pidx(int k, int i, uint32_t s) {
+    return blk_base(s) + (size_t)i * (2 * kBlk) + (size_t)k;
+}
 // elements of one state (the last block is padded)
 __host__ __device__ __forceinline__ size_t state_elems(long long N) {
     return (size_t)((N + kBlk - 1) / kBlk) * (size_t)(2 * Q * kBlk);
@@ -101,9 +104,7 @@ __device__ __forceinline__ void pull(const S* __restrict__ src, const Geom& g, c
         if constexpr (MASK && i != 0) {
             if (flags & (1u << i)) { idx = P.own; pop = Vel<i>::opp; }
         }
-#pragma unroll
-        for (int k = 0; k < 2; ++k)
-            d[k][i] = Store<S>::ld(src + pidx(k * Q + pop, idx));
+        Store<S>::ld2(src + pidx(0, pop, idx), d[0][i], d[1][i]);
     });
 }
 
@@ -143,17 +144,21 @@ __device__ __forceinline__ void sums(const float (&d)[2][Q], float& dA, float& d
 // Equilibrium deviation: f^eq_i - w_i rho0 = w_i [(rho - rho0) + rho (3 c.u
 // + 4.5 (c.u)^2 - 1.5 u.u)] (Eq. LEQ with c_s^2 = 1/3); the stored value is
 // (1 - omega) d_i + omega (f^eq_i - w_i rho0).
-// With Z, a lane with zero set stores 0 in every slot (a solid node).
+// With Z, a lane with zero set stores 0 in every slot (a solid node). Both
+// components of a velocity are stored as one pair: component A's outputs are
+// computed first (each replaces its input, which is dead after), then B's,
+// each stored with its A partner.
 template <typename S, bool Z = false>
 __device__ __forceinline__ void collide_store(const float (&d)[2][Q], const Phys& p, float dA, float dB,
                                               const float (&j)[3], const float (&SA)[3],
                                               const float (&SB)[3], S* __restrict__ dst,
                                               const Geom& g, int own, bool zero = false) {
-    auto put = [&](S* a, float v) { Store<S>::st(a, (Z && zero) ? 0.f : v); };
     const float rA = p.rho0[0] + dA, rB = p.rho0[1] + dB;
     const float inv = 1.0f / (rA + rB);
     const float up[3] = {j[0] * inv, j[1] * inv, j[2] * inv};
     const float om1 = 1.0f - p.omega;
+    float gA[Q];
+    S* out = dst + blk_base((uint32_t)own);
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const float (&Sk)[3] = (k == 0) ? SB : SA;
@@ -168,11 +173,16 @@ __device__ __forceinline__ void collide_store(const float (&d)[2][Q], const Phys
         // odd in c (3 w rho c.u)
         const float wr1 = p.omega * (1.0f / 18.0f) * rk, wd1 = p.omega * (1.0f / 18.0f) * drk;
         const float wr2 = p.omega * (1.0f / 36.0f) * rk, wd2 = p.omega * (1.0f / 36.0f) * drk;
-        S* out = dst + blk_base(own) + k * Q * kBlk;
-        {
-            const float eq0 = p.omega * (1.0f / 3.0f) * (drk - rk * uu15);
-            put(out, om1 * d[k][0] + eq0);
-        }
+        auto put = [&](int i, float v) {
+            if (k == 0) {
+                gA[i] = v;
+            } else {
+                float a = gA[i], b = v;
+                if (Z && zero) a = b = 0.f;
+                Store<S>::st2(out + i * (2 * kBlk), a, b);
+            }
+        };
+        put(0, om1 * d[k][0] + p.omega * (1.0f / 3.0f) * (drk - rk * uu15));
         static_for<0, 9>([&](auto M) {
             constexpr int i = 2 * decltype(M)::value + 1;   // (i, i + 1) opposite
             float cu = 0.f;
@@ -183,8 +193,8 @@ __device__ __forceinline__ void collide_store(const float (&d)[2][Q], const Phys
             const float wr = axis ? wr1 : wr2, wd = axis ? wd1 : wd2;
             const float even = wr * (4.5f * cu * cu - uu15) + wd;
             const float odd = 3.0f * wr * cu;
-            put(out + i * kBlk, om1 * d[k][i] + (even + odd));
-            put(out + (i + 1) * kBlk, om1 * d[k][i + 1] + (even - odd));
+            put(i, om1 * d[k][i] + (even + odd));
+            put(i + 1, om1 * d[k][i + 1] + (even - odd));
         });
     }
 }

@@ -32,34 +32,32 @@ __global__ void flags_kernel(const uint8_t* __restrict__ mask, uint32_t* __restr
     flags[s] = f;
 }
 
-// One thread per node. The read slots (population i at fluid x) and the
-// written slots (population opp(i) at solid x + c_i) are disjoint, so the
-// read and write views are restrict-qualified and every load of a node is in
-// flight before its first store.
+// One thread per node. The read slots (velocity i at fluid x) and the
+// written slots (velocity opp(i) at solid x + c_i) are disjoint, so the read
+// and write views are restrict-qualified and every load of a node is in
+// flight before its first store. Both components move as one pair.
 template <typename S>
 __global__ void reflect_kernel(const S* __restrict__ in, S* __restrict__ out,
                                const uint32_t* __restrict__ flags, Geom g) {
+    using P = typename Store<S>::Pair;
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= g.N) return;
     const uint32_t fl = __ldg(flags + s);
     if ((fl & kSolid) || !(fl & kNbSolidMask)) return;
     int x, y, z;
     site_xyz(s, g, x, y, z);
-    S v[2][Q];
+    P v[Q];
     static_for<1, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        if (fl & (1u << Vel<i>::opp)) {   // x - c_opp(i) = x + c_i is solid
-#pragma unroll
-            for (int k = 0; k < 2; ++k) v[k][i] = in[pidx(k * Q + i, s)];
-        }
+        if (fl & (1u << Vel<i>::opp))   // x - c_opp(i) = x + c_i is solid
+            v[i] = __ldg(reinterpret_cast<const P*>(in + pidx(0, i, (uint32_t)s)));
     });
     static_for<1, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         constexpr int o = Vel<i>::opp;
         if (fl & (1u << o)) {
             const long long t = nb_index<i>(g, x, y, z);
-#pragma unroll
-            for (int k = 0; k < 2; ++k) out[pidx(k * Q + o, t)] = v[k][i];
+            *reinterpret_cast<P*>(out + pidx(0, o, (uint32_t)t)) = v[i];
         }
     });
 }
@@ -88,21 +86,21 @@ __global__ void unstream_kernel(S* __restrict__ dst, const uint32_t* __restrict_
         // destination neighbour y + c_j is solid <=> flag bit opp(j) (y - c_opp(j))
         const bool nb_solid = (j != 0) && (fl & (1u << Vel<j>::opp));
         const bool back = nb_solid && !solid;
+        S* out = dst + pidx(0, j, (uint32_t)s);
         if (solid && (j == 0 || nb_solid)) {   // not read by any fluid node
-#pragma unroll
-            for (int k = 0; k < 2; ++k) Store<S>::st(dst + pidx(k * Q + j, s), 0.f);
+            Store<S>::st2(out, 0.f, 0.f);
             return;
         }
         const int tx = Vel<j>::x == 1 ? xp : (Vel<j>::x == -1 ? xm : x);
         const int ty = Vel<j>::y == 1 ? yp : (Vel<j>::y == -1 ? ym : y);
         const int tz = Vel<j>::z == 1 ? zp : (Vel<j>::z == -1 ? zm : z);
         const long long t = back ? s : (tx + (long long)g.nx * (ty + (long long)g.ny * tz));
+        float dev[2];
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
-            float dev;
             if constexpr (FROM_F) {
                 const int pop = back ? Vel<j>::opp : j;
-                dev = f[(size_t)(k * Q + pop) * g.N + t] - wgt<j>() * p.rho0[k];
+                dev[k] = f[(size_t)(k * Q + pop) * g.N + t] - wgt<j>() * p.rho0[k];
             } else {
                 const float r = (k == 0 ? rhoA : rhoB)[t];
                 float uu = 0.f, cu = 0.f;
@@ -112,10 +110,10 @@ __global__ void unstream_kernel(S* __restrict__ dst, const uint32_t* __restrict_
                     cu = Vel<j>::x * u0 + Vel<j>::y * u1 + Vel<j>::z * u2;
                     if (back) cu = -cu;   // velocity opp(j) at node y
                 }
-                dev = wgt<j>() * ((r - p.rho0[k]) + r * (cu * (3.0f + 4.5f * cu) - 1.5f * uu));
+                dev[k] = wgt<j>() * ((r - p.rho0[k]) + r * (cu * (3.0f + 4.5f * cu) - 1.5f * uu));
             }
-            Store<S>::st(dst + pidx(k * Q + j, s), dev);
         }
+        Store<S>::st2(out, dev[0], dev[1]);
     });
 }
 

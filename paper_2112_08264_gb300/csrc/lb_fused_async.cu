@@ -17,8 +17,8 @@
 //     (own node and halo node) in a 4-plane ring, keeps its own populations in
 //     registers, and after one barrier collides the previous plane with the 18
 //     neighbour densities from the ring.
-// 16-bit storage: each copy fetches the aligned 32-bit word holding the
-// element; a per-node bit mask records which half is the element.
+// Each copy fetches one velocity's (A, B) component pair: 8 bytes for FP32,
+// one 4-byte word for FP16/BF16.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -39,6 +39,15 @@ __device__ __forceinline__ int wrap_any(int a, int n) {
 __device__ __forceinline__ void cp_async4(uint32_t saddr, const void* gptr) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(saddr), "l"(gptr) : "memory");
 }
+__device__ __forceinline__ void cp_async8(uint32_t saddr, const void* gptr) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(saddr), "l"(gptr) : "memory");
+}
+// copy of one component pair (2 elements)
+template <typename S>
+__device__ __forceinline__ void cp_async_pair(uint32_t saddr, const S* gptr) {
+    if constexpr (sizeof(S) == 4) cp_async8(saddr, gptr);
+    else cp_async4(saddr, gptr);
+}
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait() {
@@ -53,44 +62,14 @@ __device__ __forceinline__ void cp_wait_n(int n) {
     }
 }
 
-template <typename S> struct Word {
-    // 4-byte source address of element pointer p, and which 16-bit half holds it
-    static __device__ __forceinline__ const void* addr(const S* p) { return p; }
-    static __device__ __forceinline__ unsigned half(const S*) { return 0u; }
-    static __device__ __forceinline__ float value(uint32_t w, unsigned) { return __uint_as_float(w); }
-};
-template <> struct Word<__half> {
-    static __device__ __forceinline__ const void* addr(const __half* p) {
-        return reinterpret_cast<const void*>(reinterpret_cast<uintptr_t>(p) & ~(uintptr_t)3);
-    }
-    static __device__ __forceinline__ unsigned half(const __half* p) {
-        return (unsigned)((reinterpret_cast<uintptr_t>(p) >> 1) & 1u);
-    }
-    static __device__ __forceinline__ float value(uint32_t w, unsigned h) {
-        return __half2float(__ushort_as_half((unsigned short)(w >> (16u * h))));
-    }
-};
-template <> struct Word<__nv_bfloat16> {
-    static __device__ __forceinline__ const void* addr(const __nv_bfloat16* p) {
-        return reinterpret_cast<const void*>(reinterpret_cast<uintptr_t>(p) & ~(uintptr_t)3);
-    }
-    static __device__ __forceinline__ unsigned half(const __nv_bfloat16* p) {
-        return (unsigned)((reinterpret_cast<uintptr_t>(p) >> 1) & 1u);
-    }
-    static __device__ __forceinline__ float value(uint32_t w, unsigned h) {
-        return __bfloat162float(__ushort_as_bfloat16((unsigned short)(w >> (16u * h))));
-    }
-};
-
 struct Smem {
-    uint32_t* stage;            // [nst][38][ns] words
+    unsigned char* stage;       // [nst][19][ns] component pairs
     float2* ring;               // [4][tymax + 2][kTX + 2]
     uint32_t* sflag;            // [nst][ns] flag words of the copied nodes
-    unsigned long long* shalf;  // [nst][ns] half-select bits (16-bit storage)
 };
 
 // Issue the copies of node (x, y, z) into slot `slot` of stage `st`; records
-// its flag word and half-select bits. Solid nodes copy nothing.
+// its flag word. Solid nodes copy nothing.
 template <typename S, bool MASK>
 __device__ __forceinline__ void issue_node(const S* __restrict__ src, const uint32_t* __restrict__ flags,
                                            const Geom& g, const AsyncPlan& P, const Smem& sm, int st, int slot,
@@ -103,8 +82,8 @@ __device__ __forceinline__ void issue_node(const S* __restrict__ src, const uint
         sm.sflag[st * P.ns + slot] = fl;
         if (fl & kSolid) return;
     }
-    unsigned long long hb = 0ull;
-    uint32_t* base = sm.stage + (size_t)st * 2 * Q * P.ns + slot;
+    constexpr int PB = 2 * (int)sizeof(S);
+    const uint32_t base = (uint32_t)__cvta_generic_to_shared(sm.stage + ((size_t)st * Q * P.ns + slot) * PB);
     static_for<0, Q>([&](auto II) {
         constexpr int i = decltype(II)::value;
         int idx = I.src[i];
@@ -112,14 +91,8 @@ __device__ __forceinline__ void issue_node(const S* __restrict__ src, const uint
         if constexpr (MASK && i != 0) {
             if (fl & (1u << i)) { idx = I.own; pop = Vel<i>::opp; }
         }
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const S* ep = src + pidx(k * Q + pop, idx);
-            cp_async4((uint32_t)__cvta_generic_to_shared(base + (size_t)(k * Q + i) * P.ns), Word<S>::addr(ep));
-            hb |= (unsigned long long)Word<S>::half(ep) << (k * Q + i);
-        }
+        cp_async_pair<S>(base + (uint32_t)(i * P.ns * PB), src + pidx(0, pop, idx));
     });
-    if constexpr (sizeof(S) == 2) sm.shalf[st * P.ns + slot] = hb;
 }
 
 // Read the landed copies of a slot into d (deviations) and return the
@@ -132,14 +105,9 @@ __device__ __forceinline__ float2 consume_node(const AsyncPlan& P, const Smem& s
         solid = (sm.sflag[st * P.ns + slot] & kSolid) != 0u;
         if (solid) return make_float2(-p.rho0[0], -p.rho0[1]);
     }
-    unsigned long long hb = 0ull;
-    if constexpr (sizeof(S) == 2) hb = sm.shalf[st * P.ns + slot];
-    const uint32_t* base = sm.stage + (size_t)st * 2 * Q * P.ns + slot;
+    const S* base = reinterpret_cast<const S*>(sm.stage) + ((size_t)st * Q * P.ns + slot) * 2;
 #pragma unroll
-    for (int k = 0; k < 2; ++k)
-#pragma unroll
-        for (int i = 0; i < Q; ++i)
-            d[k][i] = Word<S>::value(base[(size_t)(k * Q + i) * P.ns], (unsigned)((hb >> (k * Q + i)) & 1ull));
+    for (int i = 0; i < Q; ++i) Store<S>::lds2(base + (size_t)i * P.ns * 2, d[0][i], d[1][i]);
     return make_float2(dens_sum(d[0]), dens_sum(d[1]));
 }
 
@@ -149,10 +117,9 @@ fused_async_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_
                    float* __restrict__ mom_out, Geom g, Phys p, AsyncPlan P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem sm;
-    sm.stage = reinterpret_cast<uint32_t*>(smem_raw);
-    sm.ring = reinterpret_cast<float2*>(sm.stage + (size_t)P.nst * 2 * Q * P.ns);
+    sm.stage = smem_raw;
+    sm.ring = reinterpret_cast<float2*>(sm.stage + (size_t)P.nst * Q * P.ns * 2 * sizeof(S));
     sm.sflag = reinterpret_cast<uint32_t*>(sm.ring + 4 * (P.tymax + 2) * (kTX + 2));
-    sm.shalf = reinterpret_cast<unsigned long long*>(sm.sflag + (MASK ? P.nst * P.ns : 0));
     const int RW = kTX + 2, RH = P.tymax + 2;
     auto ring_at = [&](int slot, int ly, int lx) -> float2& { return sm.ring[(slot * RH + ly + 1) * RW + lx + 1]; };
 
@@ -236,23 +203,27 @@ fused_async_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_
 }
 
 // ---------------------------------------------------------------------------
-// Box variant (used when nx is a multiple of the 16-byte chunk width): per
-// plane and population the block copies one box of rows -- the tile and its
-// halo shifted by -c_i -- in 16-byte chunks, cooperatively, each chunk's
-// source wrapped periodically on its own (a chunk never straddles the wrap
-// since nx and the tile origin are multiples of the chunk width). A stage is
-// laid out [box row][population][column], so the pulled value of node
-// (lx, ly) for population (k, i) sits at row ly + 1, column lx + PAD - c_ix:
-// one shared-memory load at a compile-time offset from a per-node base.
+// Box variant (used when nx is a multiple of 4): per plane and velocity the
+// block copies one box of rows -- the tile and its halo shifted by -c_i, both
+// components -- in 16-byte chunks, cooperatively, each chunk's source wrapped
+// periodically on its own (a chunk never straddles the wrap since nx and the
+// tile origin are multiples of the chunk width, nor a storage block). A stage
+// is laid out [box row][velocity][column][component], so the pulled pair of
+// node (lx, ly) for velocity i sits at row ly + 1, column lx + PAD - c_ix: one
+// shared-memory vector load at a compile-time offset from a per-node base.
 
 template <typename S> struct BoxGeo {
-    static constexpr int CW = 16 / (int)sizeof(S);   // elements per 16-byte chunk
-    static constexpr int PAD = CW;                   // box columns left of the tile
-    static constexpr int BW = kTX + 2 * PAD;         // box width (elements)
-    static constexpr int CPR = BW / CW;              // chunks per box row
-    // stage row stride (elements): the 38 boxes of a row plus 16 bytes so that
-    // vertically adjacent nodes (halo columns) fall in different banks
-    static constexpr int ROW = 2 * Q * BW + CW;
+    static constexpr int CS = 16 / (2 * (int)sizeof(S));   // sites per 16-byte chunk
+    static constexpr int PAD = CS;                         // box columns left of the tile
+    static constexpr int BW = kTX + 2 * PAD;               // box width (sites)
+    static constexpr int CPR = BW / CS;                    // chunks per velocity and box row
+    static constexpr int VS = 2 * BW;                      // velocity stride in a stage row (elements)
+    // stage row stride (elements): the 19 boxes of a row, padded to 16 bytes
+    // mod 128 so that the column-halo nodes of consecutive rows spread over
+    // the banks
+    static constexpr int ROW0B = Q * VS * (int)sizeof(S);
+    static constexpr int ROW = (ROW0B + ((16 - ROW0B % 128) + 128) % 128) / (int)sizeof(S);
+    static_assert((ROW * (int)sizeof(S)) % 16 == 0, "stage rows must stay 16-byte aligned");
 };
 
 __device__ __forceinline__ void cp_async16(uint32_t saddr, const void* gptr) {
@@ -303,17 +274,17 @@ fused_box_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t*
 
     auto plane_of = [&](int e) { return wrap_any(z0 - 1 + e, g.nz); };
 
-    // Copier thread t (< RH * CPR) owns chunk (row jr, column jc) of all 38
+    // Copier thread t (< RH * CPR) owns chunk (row jr, column jc) of all 19
     // boxes. Its wrapped source offsets within a plane depend only on c_iy
     // and are computed once; on masked grids threads t < RH * 10 also copy
     // one 4-word chunk of the flag box.
     const bool copier = t < RH * B::CPR;
     const int jr = t / B::CPR, jc = t - (t / B::CPR) * B::CPR;
-    const int xs_chunk = wrap_any(x0 - B::PAD + jc * B::CW, g.nx);
+    const int xs_chunk = wrap_any(x0 - B::PAD + jc * B::CS, g.nx);
     const int yoff_m = wrap_any(y0 + jr, g.ny) * g.nx + xs_chunk;       // c_iy = -1
     const int yoff_0 = wrap_any(y0 - 1 + jr, g.ny) * g.nx + xs_chunk;   // c_iy =  0
     const int yoff_p = wrap_any(y0 - 2 + jr, g.ny) * g.nx + xs_chunk;   // c_iy = +1
-    const int sdst = jr * B::ROW + jc * B::CW;
+    const int sdst = jr * B::ROW + jc * B::CS * 2;
     const bool fcopier = MASK && t < RH * 10;
     int foff = 0, fdst = 0;
     if (fcopier) {
@@ -331,13 +302,13 @@ fused_box_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t*
                 const size_t pz_0 = (size_t)z * g.plane;
                 const size_t pz_p = (size_t)wrap_dec(z, g.nz) * g.plane;
                 const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(stage_base(st) + sdst);
-                static_for<0, 2 * Q>([&](auto PP) {
-                    constexpr int pop = decltype(PP)::value;
-                    constexpr int i = pop % Q;
+                static_for<0, Q>([&](auto II) {
+                    constexpr int i = decltype(II)::value;
                     const size_t pz = Vel<i>::z < 0 ? pz_m : (Vel<i>::z > 0 ? pz_p : pz_0);
                     const int yo = Vel<i>::y < 0 ? yoff_m : (Vel<i>::y > 0 ? yoff_p : yoff_0);
-                    // a chunk starts at a multiple of CW and so lies inside one block
-                    cp_async16(sbase + pop * B::BW * (int)sizeof(S), src + blk_base((uint32_t)(pz + yo)) + pop * kBlk);
+                    // a chunk starts at a multiple of CS sites and so lies inside one block
+                    cp_async16(sbase + i * B::VS * (int)sizeof(S),
+                               src + blk_base((uint32_t)(pz + yo)) + i * (2 * kBlk));
                 });
             }
             if constexpr (MASK) {
@@ -355,11 +326,10 @@ fused_box_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t*
     // (solid lanes read finite placeholders and report psi = 0)
     auto read_node = [&](int st, int lx, int ly, float (&d)[2][Q], uint32_t& fl) -> float2 {
         fl = MASK ? stage_flags(st)[(ly + 1) * 40 + lx + 4] : 0u;
-        const S* nb = stage_base(st) + (ly + 1) * B::ROW + lx + B::PAD;
+        const S* nb = stage_base(st) + (ly + 1) * B::ROW + (lx + B::PAD) * 2;
         static_for<0, Q>([&](auto II) {
             constexpr int i = decltype(II)::value;
-#pragma unroll
-            for (int k = 0; k < 2; ++k) d[k][i] = Store<S>::to_f(nb[(k * Q + i) * B::BW - Vel<i>::x]);
+            Store<S>::lds2(nb + i * B::VS - 2 * Vel<i>::x, d[0][i], d[1][i]);
         });
         if (MASK && (fl & kSolid)) return make_float2(-p.rho0[0], -p.rho0[1]);
         return make_float2(dens_sum(d[0]), dens_sum(d[1]));
@@ -492,8 +462,10 @@ AsyncPlan plan_fused_async(int nx, int ny, int nz, int sm_count, int prec, bool 
     double best_cost = 1e300;
     const int ncols = (nx + kTX - 1) / kTX;
     const int esize = prec == 0 ? 4 : 2;
-    const int cw = 16 / esize;
-    const bool box = (nx % cw) == 0 && (nx % 4) == 0;   // chunks of populations and of flag words
+    // chunks of component pairs (2 or 4 sites) and of flag words (4 sites)
+    const bool box = (nx % 4) == 0;
+    const int cpr = prec == 0 ? BoxGeo<float>::CPR : BoxGeo<__half>::CPR;
+    const size_t row_bytes = prec == 0 ? (size_t)BoxGeo<float>::ROW * 4 : (size_t)BoxGeo<__half>::ROW * 2;
     const int rmin = (ny + kMaxTY - 1) / kMaxTY;
     for (int R = rmin; R <= ny; ++R) {
         const int tymax = (ny + R - 1) / R;
@@ -501,10 +473,9 @@ AsyncPlan plan_fused_async(int nx, int ny, int nz, int sm_count, int prec, bool 
         const int threads = kTX * tymax;
         const int ns = threads + 2 * (kTX + 2) + 2 * tymax;
         if (threads < 2 * (kTX + 2) + 2 * tymax) continue;   // every halo node needs a thread
-        if (box && threads < (tymax + 2) * ((kTX + 2 * cw) / cw)) continue;   // a chunk per copier thread
-        const size_t stage = box ? (size_t)(tymax + 2) * (2 * Q * (kTX + 2 * cw) + cw) * esize +
-                                       (masked ? (size_t)(tymax + 2) * 40 * 4 : 0)
-                                 : (size_t)2 * Q * ns * 4 + (masked ? (size_t)ns * 4 : 0) + (prec != 0 ? (size_t)ns * 8 : 0);
+        if (box && threads < (tymax + 2) * cpr) continue;   // a chunk per copier thread
+        const size_t stage = box ? (size_t)(tymax + 2) * row_bytes + (masked ? (size_t)(tymax + 2) * 40 * 4 : 0)
+                                 : (size_t)Q * ns * 2 * esize + (masked ? (size_t)ns * 4 : 0);
         const size_t ring = (size_t)4 * (tymax + 2) * (kTX + 2) * 8;
         if (smem_limit < ring + 2 * stage) continue;
         int nst = (int)((smem_limit - ring) / stage);
