@@ -199,15 +199,23 @@ __device__ __forceinline__ void collide_store(const float (&d)[2][Q], const Phys
     }
 }
 
-// Per-node moments kept by the adjoint's recompute, 11 fields [c][s]:
-// drho^A, drho^B, j (3), S^A (3), S^B (3). Written at fluid nodes only.
+// Per-node moments kept by the adjoint's recompute, 11 fields: drho^A,
+// drho^B, j (3), S^A (3), S^B (3). Written at fluid nodes only, blocked like
+// the populations: field c of site s at mom_base(s) + c * kBlk.
 constexpr int kMom = 11;
+__host__ __device__ __forceinline__ size_t mom_base(uint32_t s) {
+    return (size_t)(s / (uint32_t)kBlk) * (size_t)(kMom * kBlk) + (size_t)(s % (uint32_t)kBlk);
+}
+__host__ __device__ __forceinline__ size_t mom_elems(long long N) {
+    return (size_t)((N + kBlk - 1) / kBlk) * (size_t)(kMom * kBlk);
+}
 __device__ __forceinline__ void store_moments(float* __restrict__ mom, const Geom& g, long long own, float dA,
                                               float dB, const float (&j)[3], const float (&SA)[3],
                                               const float (&SB)[3]) {
     const float v[kMom] = {dA, dB, j[0], j[1], j[2], SA[0], SA[1], SA[2], SB[0], SB[1], SB[2]};
+    float* m = mom + mom_base((uint32_t)own);
 #pragma unroll
-    for (int c = 0; c < kMom; ++c) mom[(size_t)c * g.N + own] = v[c];
+    for (int c = 0; c < kMom; ++c) m[c * kBlk] = v[c];
 }
 
 // Density deviations dpsi^k = psi^k - rho0^k of node (x, y, z): sum_i d_i^k at

@@ -31,7 +31,7 @@ struct StepLaunch {
     void* dst;
     const uint32_t* flags;    // nullptr = no solid nodes
     float* rho;               // density scratch (two-pass), 2N floats
-    float* mom_out;           // optional: per-node moments of the source state (kMom x N, fluid nodes)
+    float* mom_out;           // optional: per-node moments of the source state (mom_elems(N), fluid nodes)
     Geom g;
     Phys p;
     int zsplit;               // register fused kernel: z-chunks per tile column

@@ -27,6 +27,9 @@ namespace {
 
 constexpr int kAux = 11;   // W[3], q[2], sigma^A[3], sigma^B[3]
 constexpr int kTX = 32;
+// tile rows of the box kernel: two stages of its boxes fit in shared memory
+// for about 11 rows, and 12 rows (384 threads) leave 168 registers a thread
+constexpr int kAdjMaxTY = 12;
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -40,10 +43,10 @@ struct AdjBufs {
 AdjBufs carve(char* adj, size_t N, int K) {
     AdjBufs b;
     size_t off = 0;
-    b.lam[0] = reinterpret_cast<float*>(adj + off); off += a256(2 * Q * N * 4);
-    b.lam[1] = reinterpret_cast<float*>(adj + off); off += a256(2 * Q * N * 4);
+    b.lam[0] = reinterpret_cast<float*>(adj + off); off += a256(state_elems((long long)N) * 4);
+    b.lam[1] = reinterpret_cast<float*>(adj + off); off += a256(state_elems((long long)N) * 4);
     b.aux = reinterpret_cast<float*>(adj + off); off += a256((size_t)kAux * N * 4);
-    b.segmom = reinterpret_cast<float*>(adj + off); off += a256((size_t)K * kMom * N * 4);
+    b.segmom = reinterpret_cast<float*>(adj + off); off += a256((size_t)K * mom_elems((long long)N) * 4);
     b.gacc = reinterpret_cast<double*>(adj + off);
     return b;
 }
@@ -59,7 +62,8 @@ __device__ __forceinline__ void site_xyz(long long s, const Geom& g, int& x, int
     z = (int)(s / g.plane);
 }
 
-// mu_i(x) = lambda_i(x + c_i) if x + c_i is fluid, else lambda_opp(i)(x)
+// mu_i(x) = lambda_i(x + c_i) if x + c_i is fluid, else lambda_opp(i)(x).
+// lambda is stored like the populations (blocked, (A, B) pairs; pidx).
 template <bool MASK>
 __device__ __forceinline__ void gather_mu(const float* __restrict__ lam, const Geom& g, int x, int y, int z,
                                           long long own, uint32_t fl, float (&mu)[2][Q]) {
@@ -76,8 +80,7 @@ __device__ __forceinline__ void gather_mu(const float* __restrict__ lam, const G
         if constexpr (MASK && i != 0) {
             if (fl & (1u << Vel<i>::opp)) { t = own; pop = Vel<i>::opp; }
         }
-#pragma unroll
-        for (int k = 0; k < 2; ++k) mu[k][i] = __ldg(lam + (size_t)(k * Q + pop) * g.N + t);
+        Store<float>::ld2(lam + pidx(0, pop, (uint32_t)t), mu[0][i], mu[1][i]);
     });
 }
 
@@ -169,7 +172,7 @@ adj_pass_a(const float* __restrict__ mom, const float* __restrict__ lam, const u
         gather_mu<MASK>(lam, g, x, y, z, s, fl, mu);
         float mo[kMom];
 #pragma unroll
-        for (int c = 0; c < kMom; ++c) mo[c] = __ldg(mom + (size_t)c * g.N + s);
+        for (int c = 0; c < kMom; ++c) mo[c] = __ldg(mom + mom_base((uint32_t)s) + c * kBlk);
         float W[3], q[2], sA[3], sB[3], dG;
         adj_node(mo, mu, p, W, q, sA, sB, dG);
         const float out[kAux] = {W[0], W[1], W[2], q[0], q[1], sA[0], sA[1], sA[2], sB[0], sB[1], sB[2]};
@@ -190,8 +193,9 @@ adj_pass_b(const float* __restrict__ lam_in, const float* __restrict__ aux, cons
     site_xyz(s, g, x, y, z);
     uint32_t fl = 0;
     if constexpr (MASK) fl = flags[s];
+    float* out = lam_out + blk_base((uint32_t)s);
     if (fl & kSolid) {
-        for (int j = 0; j < 2 * Q; ++j) lam_out[(size_t)j * g.N + s] = 0.f;
+        for (int i = 0; i < Q; ++i) Store<float>::st2(out + i * (2 * kBlk), 0.f, 0.f);
         return;
     }
     float mu[2][Q];
@@ -218,17 +222,26 @@ adj_pass_b(const float* __restrict__ lam_in, const float* __restrict__ aux, cons
     });
     static_for<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-#pragma unroll
-        for (int k = 0; k < 2; ++k) lam_out[(size_t)(k * Q + i) * g.N + s] = mu[k][i] + h[k];
+        Store<float>::st2(out + i * (2 * kBlk), mu[0][i] + h[0], mu[1][i] + h[1]);
     });
 }
 
 // ---- fused box adjoint ----
 
-constexpr int kBW = 40;               // box width (floats): 4 left of the tile, 32, 4 right
-constexpr int kCPR = kBW / 4;         // 16-byte chunks per box row
-constexpr int kBoxes = 2 * Q + kMom;  // lambda populations + moment fields
-constexpr int kROW = kBoxes * kBW + 4;   // stage row stride (floats), +16 bytes against bank conflicts
+// Stage row of the box kernel: 19 lambda boxes of (A, B) pairs (2 sites per
+// 16-byte chunk, 2 sites of halo each side), then 11 moment boxes (4 sites
+// per chunk, 4 sites of halo each side), padded to 16 bytes mod 128 so that
+// the column-halo nodes of consecutive rows spread over the banks.
+constexpr int kLPAD = 2;                  // lambda box sites left of the tile
+constexpr int kLBW = kTX + 2 * kLPAD;     // lambda box width (sites)
+constexpr int kLCPR = kLBW / 2;           // 16-byte chunks per lambda box row
+constexpr int kLVS = 2 * kLBW;            // floats per lambda box row
+constexpr int kMPAD = 4;                  // moment and flag box sites left of the tile
+constexpr int kMBW = kTX + 2 * kMPAD;     // moment and flag box width (sites)
+constexpr int kMCPR = kMBW / 4;           // 16-byte chunks per moment box row
+constexpr int kROW0 = Q * kLVS + kMom * kMBW;
+constexpr int kROW = kROW0 + (((16 - (kROW0 * 4) % 128) + 128) % 128) / 4;   // stage row stride (floats)
+static_assert((kROW * 4) % 16 == 0, "stage rows must stay 16-byte aligned");
 
 __device__ __forceinline__ void cp_async16(uint32_t saddr, const void* gptr) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(gptr) : "memory");
@@ -252,13 +265,13 @@ struct Sig {
 };
 
 template <bool MASK>
-__global__ void __launch_bounds__(512, 1)
+__global__ void __launch_bounds__(kTX * kAdjMaxTY, 1)
 adj_box_kernel(const float* __restrict__ lam_in, const float* __restrict__ mom, const uint32_t* __restrict__ flags,
                float* __restrict__ lam_out, double* __restrict__ partials, Geom g, Phys p, AsyncPlan P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int RH = P.tymax + 2, RW = kTX + 2;
     const size_t box_bytes = (size_t)RH * kROW * 4;
-    const size_t stage_bytes = box_bytes + (MASK ? (size_t)RH * kBW * 4 : 0);
+    const size_t stage_bytes = box_bytes + (MASK ? (size_t)RH * kMBW * 4 : 0);
     auto stage_base = [&](int st) -> float* { return reinterpret_cast<float*>(smem_raw + (size_t)st * stage_bytes); };
     auto stage_flags = [&](int st) -> uint32_t* {
         return reinterpret_cast<uint32_t*>(smem_raw + (size_t)st * stage_bytes + box_bytes);
@@ -291,16 +304,20 @@ adj_box_kernel(const float* __restrict__ lam_in, const float* __restrict__ mom, 
         const int hgx = wrap_any(x0 + hlx, g.nx), hgy = wrap_any(y0 + hly, g.ny);
         auto plane_of = [&](int e) { return wrap_any(z0 - 1 + e, g.nz); };
 
-        // copier t (< RH * kCPR) owns chunk (jr, jc) of every box
-        const bool copier = t < RH * kCPR;
-        const int jr = t / kCPR, jc = t - (t / kCPR) * kCPR;
-        const int xs_chunk = wrap_any(x0 - 4 + jc * 4, g.nx);
-        // lambda box of population i: rows from y0 - 1 + c_iy (gather x + c_i)
+        // copier t (< RH * kLCPR) owns chunk (jr, jc) of every lambda box and,
+        // for jc < kMCPR, of every moment box and the flag box
+        const bool copier = t < RH * kLCPR;
+        const int jr = t / kLCPR, jc = t - (t / kLCPR) * kLCPR;
+        const bool mcopier = copier && jc < kMCPR;
+        const int xs_chunk = wrap_any(x0 - kLPAD + jc * 2, g.nx);
+        // lambda box of velocity i: rows from y0 - 1 + c_iy (gather x + c_i)
         const int yoff_m = wrap_any(y0 - 2 + jr, g.ny) * g.nx + xs_chunk;   // c_iy = -1
-        const int yoff_0 = wrap_any(y0 - 1 + jr, g.ny) * g.nx + xs_chunk;   // c_iy =  0 (and moments, flags)
+        const int yoff_0 = wrap_any(y0 - 1 + jr, g.ny) * g.nx + xs_chunk;   // c_iy =  0
         const int yoff_p = wrap_any(y0 + jr, g.ny) * g.nx + xs_chunk;       // c_iy = +1
+        const int moff = wrap_any(y0 - 1 + jr, g.ny) * g.nx + wrap_any(x0 - kMPAD + jc * 4, g.nx);
         const int sdst = jr * kROW + jc * 4;
-        const int fdst = jr * kBW + jc * 4;
+        const int mdst = jr * kROW + Q * kLVS + jc * 4;
+        const int fdst = jr * kMBW + jc * 4;
 
         auto issue = [&](int e) {
             if (e < L && copier) {
@@ -309,19 +326,23 @@ adj_box_kernel(const float* __restrict__ lam_in, const float* __restrict__ mom, 
                 const size_t pz_0 = (size_t)z * g.plane;
                 const size_t pz_p = (size_t)wrap_inc(z, g.nz) * g.plane;   // c_iz = +1: plane z + 1
                 const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(stage_base(st) + sdst);
-                static_for<0, 2 * Q>([&](auto PP) {
-                    constexpr int pop = decltype(PP)::value;
-                    constexpr int i = pop % Q;
+                static_for<0, Q>([&](auto II) {
+                    constexpr int i = decltype(II)::value;
                     const size_t pz = Vel<i>::z < 0 ? pz_m : (Vel<i>::z > 0 ? pz_p : pz_0);
                     const int yo = Vel<i>::y < 0 ? yoff_m : (Vel<i>::y > 0 ? yoff_p : yoff_0);
-                    cp_async16(sbase + pop * kBW * 4, lam_in + (size_t)pop * g.N + pz + yo);
+                    // a chunk of 2 sites never straddles a storage block
+                    cp_async16(sbase + i * kLVS * 4, lam_in + blk_base((uint32_t)(pz + yo)) + i * (2 * kBlk));
                 });
-                static_for<0, kMom>([&](auto CC) {
-                    constexpr int c = decltype(CC)::value;
-                    cp_async16(sbase + (2 * Q + c) * kBW * 4, mom + (size_t)c * g.N + pz_0 + yoff_0);
-                });
-                if constexpr (MASK)
-                    cp_async16((uint32_t)__cvta_generic_to_shared(stage_flags(st) + fdst), flags + pz_0 + yoff_0);
+                if (mcopier) {
+                    const uint32_t mbase = (uint32_t)__cvta_generic_to_shared(stage_base(st) + mdst);
+                    const float* msrc = mom + mom_base((uint32_t)(pz_0 + moff));
+                    static_for<0, kMom>([&](auto CC) {
+                        constexpr int c = decltype(CC)::value;
+                        cp_async16(mbase + c * kMBW * 4, msrc + c * kBlk);
+                    });
+                    if constexpr (MASK)
+                        cp_async16((uint32_t)__cvta_generic_to_shared(stage_flags(st) + fdst), flags + pz_0 + moff);
+                }
             }
             cp_commit();
         };
@@ -335,28 +356,27 @@ adj_box_kernel(const float* __restrict__ lam_in, const float* __restrict__ mom, 
             uint32_t fl = 0;
             solid = false;
             if constexpr (MASK) {
-                fl = stage_flags(st)[(ly + 1) * kBW + lx + 4];
+                fl = stage_flags(st)[(ly + 1) * kMBW + lx + kMPAD];
                 solid = (fl & kSolid) != 0u;
                 if (solid) return sg;
             }
-            const float* nb = stage_base(st) + (ly + 1) * kROW + lx + 4;
+            const float* row = stage_base(st) + (ly + 1) * kROW;
+            const float* nb = row + (lx + kLPAD) * 2;
             static_for<0, Q>([&](auto II) {
                 constexpr int i = decltype(II)::value;
-#pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    if constexpr (MASK && i != 0) {
-                        if (fl & (1u << Vel<i>::opp)) {   // x + c_i solid: lambda_opp(i) at x
-                            const size_t own = (size_t)x + (size_t)g.nx * ((size_t)y + (size_t)g.ny * z);
-                            mu[k][i] = __ldg(lam_in + (size_t)(k * Q + Vel<i>::opp) * g.N + own);
-                            continue;
-                        }
+                if constexpr (MASK && i != 0) {
+                    if (fl & (1u << Vel<i>::opp)) {   // x + c_i solid: lambda_opp(i) at x
+                        const size_t own = (size_t)x + (size_t)g.nx * ((size_t)y + (size_t)g.ny * z);
+                        Store<float>::ld2(lam_in + pidx(0, Vel<i>::opp, (uint32_t)own), mu[0][i], mu[1][i]);
+                        return;
                     }
-                    mu[k][i] = nb[(k * Q + i) * kBW + Vel<i>::x];
                 }
+                Store<float>::lds2(nb + i * kLVS + 2 * Vel<i>::x, mu[0][i], mu[1][i]);
             });
+            const float* mb = row + Q * kLVS + lx + kMPAD;
             float mo[kMom];
 #pragma unroll
-            for (int c = 0; c < kMom; ++c) mo[c] = nb[(2 * Q + c) * kBW];
+            for (int c = 0; c < kMom; ++c) mo[c] = mb[c * kMBW];
             float W[3], q[2];
             adj_node(mo, mu, p, W, q, sg.a, sg.b, dG);
             local_part(mu, p, W, q);
@@ -388,10 +408,10 @@ adj_box_kernel(const float* __restrict__ lam_in, const float* __restrict__ mom, 
             if (e >= 2 && active) {
                 const int zc = plane_of(e - 1);
                 const size_t own = (size_t)gx + (size_t)g.nx * ((size_t)gy + (size_t)g.ny * zc);
-                float* out = lam_out + own;
+                float* out = lam_out + blk_base((uint32_t)own);
                 if (solid_cur) {
 #pragma unroll
-                    for (int j = 0; j < 2 * Q; ++j) out[(size_t)j * g.N] = 0.f;
+                    for (int i = 0; i < Q; ++i) Store<float>::st2(out + i * (2 * kBlk), 0.f, 0.f);
                 } else {
                     // h^k = sum_{i>=1} w_i c_i . sigma^k(x - c_i); x - c_i lies in
                     // plane (e - 1) - c_iz, i.e. ring slot e - 1 - c_iz
@@ -409,8 +429,7 @@ adj_box_kernel(const float* __restrict__ lam_in, const float* __restrict__ mom, 
                     });
                     static_for<0, Q>([&](auto II) {
                         constexpr int i = decltype(II)::value;
-#pragma unroll
-                        for (int k = 0; k < 2; ++k) __stcs(out + (size_t)(k * Q + i) * g.N, cur[k][i] + h[k]);
+                        Store<float>::st2(out + i * (2 * kBlk), cur[0][i] + h[0], cur[1][i] + h[1]);
                     });
                 }
             }
@@ -433,10 +452,8 @@ __global__ void adj_seed(const float* __restrict__ dLA, const float* __restrict_
     const bool fluid = !(flags && (flags[s] & kSolid));
     const float a = (fluid && dLA) ? dLA[s] : 0.f;
     const float b = (fluid && dLB) ? dLB[s] : 0.f;
-    for (int i = 0; i < Q; ++i) {
-        lam[(size_t)i * g.N + s] = a;
-        lam[(size_t)(Q + i) * g.N + s] = b;
-    }
+    float* out = lam + blk_base((uint32_t)s);
+    for (int i = 0; i < Q; ++i) Store<float>::st2(out + i * (2 * kBlk), a, b);
 }
 
 // dL/drho^k_0(x) = sum_i w_i lambda_0^k_i(x) (f_0 = f^eq(rho^k_0, 0) = w_i rho^k_0).
@@ -448,8 +465,10 @@ __global__ void adj_final(const float* __restrict__ lam, const uint32_t* __restr
     float acc[2] = {0.f, 0.f};
     static_for<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-#pragma unroll
-        for (int k = 0; k < 2; ++k) acc[k] += wgt<i>() * lam[(size_t)(k * Q + i) * g.N + s];
+        float a, b;
+        Store<float>::ld2(lam + pidx(0, i, (uint32_t)s), a, b);
+        acc[0] += wgt<i>() * a;
+        acc[1] += wgt<i>() * b;
     });
     if (gA) gA[s] = fluid ? acc[0] : 0.f;
     if (gB) gB[s] = fluid ? acc[1] : 0.f;
@@ -470,7 +489,8 @@ __global__ void __launch_bounds__(256) adj_accumulate(const double* __restrict__
 
 size_t adjoint_workspace_bytes(int nx, int ny, int nz, int K) {
     const size_t N = (size_t)nx * ny * nz;
-    return 2 * a256(2 * Q * N * 4) + a256((size_t)kAux * N * 4) + a256((size_t)K * kMom * N * 4) + 256;
+    return 2 * a256(state_elems((long long)N) * 4) + a256((size_t)kAux * N * 4) +
+           a256((size_t)K * mom_elems((long long)N) * 4) + 256;
 }
 
 AsyncPlan plan_adjoint_box(int nx, int ny, int nz, int sm_count, bool masked, size_t smem_limit) {
@@ -480,13 +500,13 @@ AsyncPlan plan_adjoint_box(int nx, int ny, int nz, int sm_count, bool masked, si
     smem_limit = smem_limit > 4096 ? smem_limit - 4096 : 0;   // room for static shared memory
     double best_cost = 1e300;
     const int ncols = (nx + kTX - 1) / kTX;
-    for (int R = (ny + 15) / 16; R <= ny; ++R) {
+    for (int R = (ny + kAdjMaxTY - 1) / kAdjMaxTY; R <= ny; ++R) {
         const int tymax = (ny + R - 1) / R;
         const int RH = tymax + 2;
         const int threads = kTX * tymax;
         if (threads < 2 * (kTX + 2) + 2 * tymax) continue;   // a thread per halo node
-        if (threads < RH * kCPR) continue;                     // a thread per chunk position
-        const size_t stage = (size_t)RH * kROW * 4 + (masked ? (size_t)RH * kBW * 4 : 0);
+        if (threads < RH * kLCPR) continue;                    // a thread per chunk position
+        const size_t stage = (size_t)RH * kROW * 4 + (masked ? (size_t)RH * kMBW * 4 : 0);
         const size_t ring = (size_t)4 * RH * (kTX + 2) * sizeof(float) * 6;
         if (smem_limit < ring + 2 * stage) continue;
         int nst = (int)((smem_limit - ring) / stage);
@@ -557,12 +577,12 @@ cudaError_t run_adjoint(const AdjointRun& R, const float* dLA, const float* dLB,
         for (int s = 0; s < Lm; ++s) {
             S.src = R.seg + (size_t)s * R.state_bytes;
             S.dst = (s + 1 < Lm) ? (void*)(R.seg + (size_t)(s + 1) * R.state_bytes) : R.scratch;
-            S.mom_out = B.segmom + (size_t)s * kMom * N;
+            S.mom_out = B.segmom + (size_t)s * mom_elems((long long)N);
             if ((e = launch_step(S, st)) != cudaSuccess) return e;
         }
         // reverse through it
         for (int s = Lm - 1; s >= 0; --s) {
-            const float* mom = B.segmom + (size_t)s * kMom * N;
+            const float* mom = B.segmom + (size_t)s * mom_elems((long long)N);
             if (box) {
                 dim3 grid(AP.ncols * AP.R, AP.zsplit, 1);
                 if (mask)
