@@ -148,11 +148,12 @@ __device__ __forceinline__ void sums(const float (&d)[2][Q], float& dA, float& d
 // components of a velocity are stored as one pair: component A's outputs are
 // computed first (each replaces its input, which is dead after), then B's,
 // each stored with its A partner.
-template <typename S, bool Z = false>
-__device__ __forceinline__ void collide_store(const float (&d)[2][Q], const Phys& p, float dA, float dB,
-                                              const float (&j)[3], const float (&SA)[3],
-                                              const float (&SB)[3], S* __restrict__ dst,
-                                              const Geom& g, int own, bool zero = false) {
+// dget(k, i) gives the pulled deviation d_i^k.
+template <typename S, bool Z = false, typename DGet>
+__device__ __forceinline__ void collide_store_g(DGet&& dget, const Phys& p, float dA, float dB,
+                                                const float (&j)[3], const float (&SA)[3],
+                                                const float (&SB)[3], S* __restrict__ dst,
+                                                const Geom& g, int own, bool zero = false) {
     const float rA = p.rho0[0] + dA, rB = p.rho0[1] + dB;
     const float inv = 1.0f / (rA + rB);
     const float up[3] = {j[0] * inv, j[1] * inv, j[2] * inv};
@@ -182,7 +183,7 @@ __device__ __forceinline__ void collide_store(const float (&d)[2][Q], const Phys
                 Store<S>::st2(out + i * (2 * kBlk), a, b);
             }
         };
-        put(0, om1 * d[k][0] + p.omega * (1.0f / 3.0f) * (drk - rk * uu15));
+        put(0, om1 * dget(k, 0) + p.omega * (1.0f / 3.0f) * (drk - rk * uu15));
         static_for<0, 9>([&](auto M) {
             constexpr int i = 2 * decltype(M)::value + 1;   // (i, i + 1) opposite
             float cu = 0.f;
@@ -193,10 +194,18 @@ __device__ __forceinline__ void collide_store(const float (&d)[2][Q], const Phys
             const float wr = axis ? wr1 : wr2, wd = axis ? wd1 : wd2;
             const float even = wr * (4.5f * cu * cu - uu15) + wd;
             const float odd = 3.0f * wr * cu;
-            put(i, om1 * d[k][i] + (even + odd));
-            put(i + 1, om1 * d[k][i + 1] + (even - odd));
+            put(i, om1 * dget(k, i) + (even + odd));
+            put(i + 1, om1 * dget(k, i + 1) + (even - odd));
         });
     }
+}
+
+template <typename S, bool Z = false>
+__device__ __forceinline__ void collide_store(const float (&d)[2][Q], const Phys& p, float dA, float dB,
+                                              const float (&j)[3], const float (&SA)[3],
+                                              const float (&SB)[3], S* __restrict__ dst,
+                                              const Geom& g, int own, bool zero = false) {
+    collide_store_g<S, Z>([&](int k, int i) { return d[k][i]; }, p, dA, dB, j, SA, SB, dst, g, own, zero);
 }
 
 // Per-node moments kept by the adjoint's recompute, 11 fields: drho^A,

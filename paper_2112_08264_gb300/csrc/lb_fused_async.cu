@@ -334,35 +334,70 @@ fused_box_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t*
         if (MASK && (fl & kSolid)) return make_float2(-p.rho0[0], -p.rho0[1]);
         return make_float2(dens_sum(d[0]), dens_sum(d[1]));
     };
+    // 16-bit storage, own node: the pairs stay packed (one word per velocity)
+    // until the collision; the momentum is taken here, from the same values
+    auto read_node_packed = [&](int st, int lx, int ly, uint32_t (&w)[Q], float (&j)[3], uint32_t& fl) -> float2 {
+        fl = MASK ? stage_flags(st)[(ly + 1) * 40 + lx + 4] : 0u;
+        const S* nb = stage_base(st) + (ly + 1) * B::ROW + (lx + B::PAD) * 2;
+        float d[2][Q];
+        static_for<0, Q>([&](auto II) {
+            if constexpr (sizeof(S) == 2) {
+                constexpr int i = decltype(II)::value;
+                w[i] = *reinterpret_cast<const uint32_t*>(nb + i * B::VS - 2 * Vel<i>::x);
+                d[0][i] = Store<S>::part(w[i], 0);
+                d[1][i] = Store<S>::part(w[i], 1);
+            }
+        });
+        momentum(d, j);
+        if (MASK && (fl & kSolid)) return make_float2(-p.rho0[0], -p.rho0[1]);
+        return make_float2(dens_sum(d[0]), dens_sum(d[1]));
+    };
 
+    // 16-bit storage (three or four stages fit): the copies of event
+    // e + nst - 1 are issued right after the first barrier of event e, into
+    // the stage read at event e - 1, so that the copier warps do that work
+    // while the halo warps read their extra node. FP32 (two stages): they are
+    // issued after the second barrier into the stage just read (event e + nst).
+    constexpr bool early = sizeof(S) == 2;
+    const int ahead = early ? P.nst - 1 : P.nst;   // events in flight
     // planes and stages advance by one per event; tracked incrementally
     const int zfirst = wrap_any(z0 - 1, g.nz);
     {
         int z = zfirst;
-        for (int e = 0; e < P.nst; ++e) {
+        for (int e = 0; e < ahead; ++e) {
             issue(e, z, e);
             z = wrap_inc(z, g.nz);
         }
     }
     int z_cur = zfirst, z_prev = zfirst, st_cur = 0;
-    int z_iss = wrap_any(z0 - 1 + P.nst, g.nz);   // plane of event e + nst
+    int z_iss = wrap_any(z0 - 1 + ahead, g.nz);   // plane of event e + ahead
     const int own_off = (ty + 1) * RW + tx + 1;   // this node's ring cell within a slot
 
-    float cur[2][Q], nxt[2][Q];
+    // own populations between their read (event e) and their collision
+    // (event e + 1): floats for FP32, packed pair words and the momentum for
+    // 16-bit storage (fewer live registers)
+    constexpr bool packed = sizeof(S) == 2;
+    float cur[2][packed ? 1 : Q], nxt[2][packed ? 1 : Q];
+    uint32_t curw[packed ? Q : 1], nxtw[packed ? Q : 1];
+    float jcur[3] = {0.f, 0.f, 0.f}, jnxt[3] = {0.f, 0.f, 0.f};
     uint32_t fl_cur = kSolid;
     for (int e = 0; e < L; ++e) {
-        cp_wait_n(P.nst - 1);
+        cp_wait_n(ahead - 1);
         __syncthreads();   // every thread's chunks of event e are visible
+        if constexpr (early) issue(e + ahead, z_iss, st_cur == 0 ? P.nst - 1 : st_cur - 1);
         const int slot = e & 3;
         uint32_t fl_nxt = kSolid;
-        if (own_row) ring[slot * RH * RW + own_off] = read_node(st_cur, tx, ty, nxt, fl_nxt);
+        if (own_row) {
+            if constexpr (packed) ring[slot * RH * RW + own_off] = read_node_packed(st_cur, tx, ty, nxtw, jnxt, fl_nxt);
+            else ring[slot * RH * RW + own_off] = read_node(st_cur, tx, ty, nxt, fl_nxt);
+        }
         if (has_halo) {
             float dh[2][Q];
             uint32_t fh;
             ring_at(slot, hly, hlx) = read_node(st_cur, hlx, hly, dh, fh);
         }
         __syncthreads();   // ring of plane e complete; stage st_cur fully read
-        issue(e + P.nst, z_iss, st_cur);
+        if constexpr (!early) issue(e + ahead, z_iss, st_cur);
         // Solid lanes run the same code and store zeros, so that every warp
         // stores whole sectors (a partly written sector costs a DRAM read);
         // the solid slots a fluid node pulls are filled afterwards by the
@@ -374,12 +409,13 @@ fused_box_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t*
             const float2* rc = ring + ((e - 1) & 3) * RH * RW + own_off;
             const float2* rp = ring + slot * RH * RW + own_off;
             float dA, dB, j[3];
-            if constexpr (sizeof(S) == 4) {
+            if constexpr (!packed) {
                 sums(cur, dA, dB, j);
             } else {   // own density deviations are already in the ring (same sums)
                 dA = rc[0].x;
                 dB = rc[0].y;
-                momentum(cur, j);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) j[a] = jcur[a];
             }
             float SA[3], SB[3];
             neighbour_sums(
@@ -390,12 +426,27 @@ fused_box_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t*
                 SA, SB);
             const bool solid = MASK && (fl_cur & kSolid);
             if (mom_out != nullptr && !solid) store_moments(mom_out, g, own, dA, dB, j, SA, SB);
-            collide_store<S, MASK>(cur, p, dA, dB, j, SA, SB, dst, g, (int)own, solid);
+            if constexpr (packed)
+                collide_store_g<S, MASK>(
+                    [&](int k, int i) {
+                        if constexpr (sizeof(S) == 2) return Store<S>::part(curw[i], k);
+                        else return 0.f;
+                    },
+                    p, dA, dB, j, SA, SB, dst, g, (int)own, solid);
+            else
+                collide_store<S, MASK>(cur, p, dA, dB, j, SA, SB, dst, g, (int)own, solid);
         }
+        if constexpr (packed) {
 #pragma unroll
-        for (int k = 0; k < 2; ++k)
+            for (int i = 0; i < Q; ++i) curw[i] = nxtw[i];
 #pragma unroll
-            for (int i = 0; i < Q; ++i) cur[k][i] = nxt[k][i];
+            for (int a = 0; a < 3; ++a) jcur[a] = jnxt[a];
+        } else {
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+#pragma unroll
+                for (int i = 0; i < Q; ++i) cur[k][i] = nxt[k][i];
+        }
         fl_cur = fl_nxt;
         z_prev = z_cur;
         z_cur = wrap_inc(z_cur, g.nz);

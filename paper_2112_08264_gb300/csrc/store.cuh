@@ -53,6 +53,10 @@ template <> struct Store<__half> {
         a = f.x;
         b = f.y;
     }
+    // component k of a pair word
+    static __device__ __forceinline__ float part(unsigned int w, int k) {
+        return __half2float(__ushort_as_half((unsigned short)(k == 0 ? (w & 0xffffu) : (w >> 16))));
+    }
     static __device__ __forceinline__ void ld2(const __half* p, float& a, float& b) {
         unpack(__ldg(reinterpret_cast<const unsigned int*>(p)), a, b);
     }
@@ -80,6 +84,10 @@ template <> struct Store<__nv_bfloat16> {
         const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w));
         a = f.x;
         b = f.y;
+    }
+    // component k of a pair word (a bf16 is the upper half of its float)
+    static __device__ __forceinline__ float part(unsigned int w, int k) {
+        return __uint_as_float(k == 0 ? (w << 16) : (w & 0xffff0000u));
     }
     static __device__ __forceinline__ void ld2(const __nv_bfloat16* p, float& a, float& b) {
         unpack(__ldg(reinterpret_cast<const unsigned int*>(p)), a, b);
