@@ -53,9 +53,10 @@ template <> struct Store<__half> {
         a = f.x;
         b = f.y;
     }
-    // component k of a pair word
+    // component k of a pair word (the conversion selects the half itself)
     static __device__ __forceinline__ float part(unsigned int w, int k) {
-        return __half2float(__ushort_as_half((unsigned short)(k == 0 ? (w & 0xffffu) : (w >> 16))));
+        const __half2 h = *reinterpret_cast<const __half2*>(&w);
+        return k == 0 ? __low2float(h) : __high2float(h);
     }
     static __device__ __forceinline__ void ld2(const __half* p, float& a, float& b) {
         unpack(__ldg(reinterpret_cast<const unsigned int*>(p)), a, b);
