@@ -89,7 +89,7 @@ __device__ __forceinline__ void gather_mu(const float* __restrict__ lam, const G
 __device__ __forceinline__ void adj_node(const float (&mo)[kMom], const float (&mu)[2][Q], const Phys& p,
                                          float (&W)[3], float (&q)[2], float (&sA)[3], float (&sB)[3], float& dG) {
     const float rA = p.rho0[0] + mo[0], rB = p.rho0[1] + mo[1];
-    const float inv = 1.0f / (rA + rB);
+    const float inv = __fdividef(1.0f, rA + rB);   // as in the forward collision
     const float up[3] = {mo[2] * inv, mo[3] * inv, mo[4] * inv};
     const float SA[3] = {mo[5], mo[6], mo[7]}, SB[3] = {mo[8], mo[9], mo[10]};
     float V[2][3], E[2];

@@ -375,21 +375,29 @@ fused_box_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t*
 
     // own populations between their read (event e) and their collision
     // (event e + 1): floats for FP32, packed pair words and the momentum for
-    // 16-bit storage (fewer live registers)
+    // 16-bit storage (fewer live registers). Two holders swap roles on
+    // alternate events (the loop is unrolled by two), so nothing is copied.
     constexpr bool packed = sizeof(S) == 2;
-    float cur[2][packed ? 1 : Q], nxt[2][packed ? 1 : Q];
-    uint32_t curw[packed ? Q : 1], nxtw[packed ? Q : 1];
-    float jcur[3] = {0.f, 0.f, 0.f}, jnxt[3] = {0.f, 0.f, 0.f};
-    uint32_t fl_cur = kSolid;
-    for (int e = 0; e < L; ++e) {
+    struct Held {
+        float d[2][packed ? 1 : Q];
+        uint32_t w[packed ? Q : 1];
+        float j[3];
+        uint32_t fl;
+    };
+    Held h0, h1;
+    h0.fl = h1.fl = kSolid;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) h0.j[a] = h1.j[a] = 0.f;
+
+    auto event = [&](int e, Held& cur, Held& nxt) {
         cp_wait_n(ahead - 1);
         __syncthreads();   // every thread's chunks of event e are visible
         if constexpr (early) issue(e + ahead, z_iss, st_cur == 0 ? P.nst - 1 : st_cur - 1);
         const int slot = e & 3;
-        uint32_t fl_nxt = kSolid;
+        nxt.fl = kSolid;
         if (own_row) {
-            if constexpr (packed) ring[slot * RH * RW + own_off] = read_node_packed(st_cur, tx, ty, nxtw, jnxt, fl_nxt);
-            else ring[slot * RH * RW + own_off] = read_node(st_cur, tx, ty, nxt, fl_nxt);
+            if constexpr (packed) ring[slot * RH * RW + own_off] = read_node_packed(st_cur, tx, ty, nxt.w, nxt.j, nxt.fl);
+            else ring[slot * RH * RW + own_off] = read_node(st_cur, tx, ty, nxt.d, nxt.fl);
         }
         if (has_halo) {
             float dh[2][Q];
@@ -401,21 +409,21 @@ fused_box_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t*
         // Solid lanes run the same code and store zeros, so that every warp
         // stores whole sectors (a partly written sector costs a DRAM read);
         // the solid slots a fluid node pulls are filled afterwards by the
-        // bounce-back pass. (The fl_cur test on unmasked FP32 grids is always
+        // bounce-back pass. (The fl test on unmasked FP32 grids is always
         // true; it is kept because that form schedules measurably faster.)
-        if (e >= 2 && active && (MASK || sizeof(S) != 4 || !(fl_cur & kSolid))) {
+        if (e >= 2 && active && (MASK || sizeof(S) != 4 || !(cur.fl & kSolid))) {
             const long long own = gx + (long long)g.nx * (gy + (long long)g.ny * z_prev);
             const float2* rm = ring + ((e - 2) & 3) * RH * RW + own_off;
             const float2* rc = ring + ((e - 1) & 3) * RH * RW + own_off;
             const float2* rp = ring + slot * RH * RW + own_off;
             float dA, dB, j[3];
             if constexpr (!packed) {
-                sums(cur, dA, dB, j);
+                sums(cur.d, dA, dB, j);
             } else {   // own density deviations are already in the ring (same sums)
                 dA = rc[0].x;
                 dB = rc[0].y;
 #pragma unroll
-                for (int a = 0; a < 3; ++a) j[a] = jcur[a];
+                for (int a = 0; a < 3; ++a) j[a] = cur.j[a];
             }
             float SA[3], SB[3];
             neighbour_sums(
@@ -424,34 +432,26 @@ fused_box_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t*
                     return r[dy * RW + dx];
                 },
                 SA, SB);
-            const bool solid = MASK && (fl_cur & kSolid);
+            const bool solid = MASK && (cur.fl & kSolid);
             if (mom_out != nullptr && !solid) store_moments(mom_out, g, own, dA, dB, j, SA, SB);
             if constexpr (packed)
                 collide_store_g<S, MASK>(
                     [&](int k, int i) {
-                        if constexpr (sizeof(S) == 2) return Store<S>::part(curw[i], k);
+                        if constexpr (sizeof(S) == 2) return Store<S>::part(cur.w[i], k);
                         else return 0.f;
                     },
                     p, dA, dB, j, SA, SB, dst, g, (int)own, solid);
             else
-                collide_store<S, MASK>(cur, p, dA, dB, j, SA, SB, dst, g, (int)own, solid);
+                collide_store<S, MASK>(cur.d, p, dA, dB, j, SA, SB, dst, g, (int)own, solid);
         }
-        if constexpr (packed) {
-#pragma unroll
-            for (int i = 0; i < Q; ++i) curw[i] = nxtw[i];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) jcur[a] = jnxt[a];
-        } else {
-#pragma unroll
-            for (int k = 0; k < 2; ++k)
-#pragma unroll
-                for (int i = 0; i < Q; ++i) cur[k][i] = nxt[k][i];
-        }
-        fl_cur = fl_nxt;
         z_prev = z_cur;
         z_cur = wrap_inc(z_cur, g.nz);
         z_iss = wrap_inc(z_iss, g.nz);
         st_cur = st_cur + 1 == P.nst ? 0 : st_cur + 1;
+    };
+    for (int e = 0; e < L; e += 2) {
+        event(e, h0, h1);
+        if (e + 1 < L) event(e + 1, h1, h0);
     }
     cp_wait<0>();
 }
