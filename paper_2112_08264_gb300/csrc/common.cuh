@@ -248,19 +248,76 @@ __device__ __forceinline__ float2 density_at(const S* __restrict__ src, const ui
     return make_float2(dens_sum(d[0]), dens_sum(d[1]));
 }
 
-// S^k = sum_{i>=1} w_i psi^k(x + c_i) c_i from a lookup of dpsi(dx, dy, dz).
-template <typename Look>
-__device__ __forceinline__ void neighbour_sums(Look&& psi, float (&SA)[3], float (&SB)[3]) {
-#pragma unroll
-    for (int a = 0; a < 3; ++a) SA[a] = SB[a] = 0.f;
-    static_for<1, Q>([&](auto I) {
-        constexpr int i = decltype(I)::value;
-        const float2 v = psi(Vel<i>::x, Vel<i>::y, Vel<i>::z);
-        constexpr float w = wgt<i>();
-        if constexpr (Vel<i>::x != 0) { SA[0] += (w * Vel<i>::x) * v.x; SB[0] += (w * Vel<i>::x) * v.y; }
-        if constexpr (Vel<i>::y != 0) { SA[1] += (w * Vel<i>::y) * v.x; SB[1] += (w * Vel<i>::y) * v.y; }
-        if constexpr (Vel<i>::z != 0) { SA[2] += (w * Vel<i>::z) * v.x; SB[2] += (w * Vel<i>::z) * v.y; }
-    });
+// Shan-Chen neighbour sums S^k = sum_{i>=1} w_i psi^k(x + c_i) c_i, in a
+// form factored by planes. For the column (x, y) of plane p (both components, .x = A,
+// .y = B):
+//   dx(p) = psi(x+1, y, p) - psi(x-1, y, p),   dy(p) = psi(x, y+1, p) - psi(x, y-1, p),
+//   t(p)  = w1 psi(x, y, p) + w2 (psi(x+1, y, p) + psi(x-1, y, p) + psi(x, y+1, p) + psi(x, y-1, p)),
+// with w1 = 1/18 (axis links) and w2 = 1/36 (diagonal links). Then, with the
+// in-plane diagonals d_pm = psi(x+1, y-1, z) etc. of the node's plane z,
+//   S_x = w1 dx(z) + w2 ((d_pp - d_mp) + (d_pm - d_mm)) + w2 (dx(z+1) + dx(z-1)),
+//   S_y = w1 dy(z) + w2 ((d_pp - d_pm) + (d_mp - d_mm)) + w2 (dy(z+1) + dy(z-1)),
+//   S_z = t(z+1) - t(z-1).
+// A kernel marching in z computes the plane quantities of a column once and
+// uses them for three nodes.
+constexpr float kW1 = 1.0f / 18.0f, kW2 = 1.0f / 36.0f;
+
+struct PlaneSums {
+    float2 dx, dy, t;
+};
+
+__device__ __forceinline__ PlaneSums plane_sums(float2 c, float2 xp, float2 xm, float2 yp, float2 ym) {
+    PlaneSums s;
+    s.dx = make_float2(xp.x - xm.x, xp.y - xm.y);
+    s.dy = make_float2(yp.x - ym.x, yp.y - ym.y);
+    s.t = make_float2(kW1 * c.x + kW2 * ((xp.x + xm.x) + (yp.x + ym.x)),
+                      kW1 * c.y + kW2 * ((xp.y + xm.y) + (yp.y + ym.y)));
+    return s;
 }
+
+__device__ __forceinline__ void force_sums(const PlaneSums& lo, const PlaneSums& mid, const PlaneSums& hi,
+                                           float2 pp, float2 mp, float2 pm, float2 mm, float (&SA)[3],
+                                           float (&SB)[3]) {
+    SA[0] = (kW1 * mid.dx.x + kW2 * ((pp.x - mp.x) + (pm.x - mm.x))) + kW2 * (hi.dx.x + lo.dx.x);
+    SB[0] = (kW1 * mid.dx.y + kW2 * ((pp.y - mp.y) + (pm.y - mm.y))) + kW2 * (hi.dx.y + lo.dx.y);
+    SA[1] = (kW1 * mid.dy.x + kW2 * ((pp.x - pm.x) + (mp.x - mm.x))) + kW2 * (hi.dy.x + lo.dy.x);
+    SB[1] = (kW1 * mid.dy.y + kW2 * ((pp.y - pm.y) + (mp.y - mm.y))) + kW2 * (hi.dy.y + lo.dy.y);
+    SA[2] = hi.t.x - lo.t.x;
+    SB[2] = hi.t.y - lo.t.y;
+}
+
+// plane quantities of plane dz (-1, 0, +1) from a lookup of dpsi(dx, dy, dz)
+template <typename Look>
+__device__ __forceinline__ PlaneSums plane_sums_at(Look&& psi, int dz) {
+    return plane_sums(psi(0, 0, dz), psi(1, 0, dz), psi(-1, 0, dz), psi(0, 1, dz), psi(0, -1, dz));
+}
+
+// S^k from a lookup of dpsi(dx, dy, dz) (the 18 neighbours of the node).
+// FACTORED: the plane form above (16-bit storage, whose box kernel reuses
+// the plane quantities); otherwise one multiply-add per link and component in
+// velocity order (FP32, where it schedules faster). Every kernel of a storage
+// type uses the same form, so the kernels of one precision give the same bits.
+template <bool FACTORED, typename Look>
+__device__ __forceinline__ void neighbour_sums(Look&& psi, float (&SA)[3], float (&SB)[3]) {
+    if constexpr (FACTORED) {
+        const PlaneSums lo = plane_sums_at(psi, -1), mid = plane_sums_at(psi, 0), hi = plane_sums_at(psi, 1);
+        force_sums(lo, mid, hi, psi(1, 1, 0), psi(-1, 1, 0), psi(1, -1, 0), psi(-1, -1, 0), SA, SB);
+    } else {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) SA[a] = SB[a] = 0.f;
+        static_for<1, Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            const float2 v = psi(Vel<i>::x, Vel<i>::y, Vel<i>::z);
+            constexpr float w = wgt<i>();
+            if constexpr (Vel<i>::x != 0) { SA[0] += (w * Vel<i>::x) * v.x; SB[0] += (w * Vel<i>::x) * v.y; }
+            if constexpr (Vel<i>::y != 0) { SA[1] += (w * Vel<i>::y) * v.x; SB[1] += (w * Vel<i>::y) * v.y; }
+            if constexpr (Vel<i>::z != 0) { SA[2] += (w * Vel<i>::z) * v.x; SB[2] += (w * Vel<i>::z) * v.y; }
+        });
+    }
+}
+
+// the form used by the kernels of storage type S
+template <typename S>
+constexpr bool kFactoredSums = sizeof(S) == 2;
 
 }  // namespace lbgb

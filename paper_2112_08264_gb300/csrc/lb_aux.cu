@@ -183,7 +183,7 @@ __global__ void moments_kernel(const S* __restrict__ src, const uint32_t* __rest
     if (oB) oB[s] = rB;
     if (!ou) return;
     float SA[3], SB[3];
-    neighbour_sums(
+    neighbour_sums<kFactoredSums<S>>(
         [&](int dx, int dy, int dz) {
             const int xx = dx > 0 ? wrap_inc(x, g.nx) : (dx < 0 ? wrap_dec(x, g.nx) : x);
             const int yy = dy > 0 ? wrap_inc(y, g.ny) : (dy < 0 ? wrap_dec(y, g.ny) : y);

@@ -183,7 +183,7 @@ fused_async_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_
                 float dA, dB, j[3];
                 sums(cur, dA, dB, j);
                 float SA[3], SB[3];
-                neighbour_sums(
+                neighbour_sums<kFactoredSums<S>>(
                     [&](int dx, int dy, int dz) {
                         const int s = dz < 0 ? sm_m : (dz > 0 ? sm_p : sm_c);
                         return ring_at(s, ty + dy, tx + dx);
@@ -386,6 +386,12 @@ fused_box_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t*
     };
     Held h0, h1;
     h0.fl = h1.fl = kSolid;
+    // 16-bit storage: plane quantities of the neighbour sums for this column,
+    // planes e - 2, e - 1 (held) and e (computed once the ring of plane e is
+    // complete); FP32 (fewer free registers) evaluates the same expressions
+    // from the ring for each node
+    PlaneSums ps_lo, ps_mid;
+    ps_lo.dx = ps_lo.dy = ps_lo.t = ps_mid.dx = ps_mid.dy = ps_mid.t = make_float2(0.f, 0.f);
 #pragma unroll
     for (int a = 0; a < 3; ++a) h0.j[a] = h1.j[a] = 0.f;
 
@@ -406,6 +412,11 @@ fused_box_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t*
         }
         __syncthreads();   // ring of plane e complete; stage st_cur fully read
         if constexpr (!early) issue(e + ahead, z_iss, st_cur);
+        PlaneSums ps_hi;
+        if constexpr (packed) {
+            const float2* rn = ring + slot * RH * RW + own_off;
+            if (own_row) ps_hi = plane_sums(rn[0], rn[1], rn[-1], rn[RW], rn[-RW]);
+        }
         // Solid lanes run the same code and store zeros, so that every warp
         // stores whole sectors (a partly written sector costs a DRAM read);
         // the solid slots a fluid node pulls are filled afterwards by the
@@ -413,9 +424,7 @@ fused_box_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t*
         // true; it is kept because that form schedules measurably faster.)
         if (e >= 2 && active && (MASK || sizeof(S) != 4 || !(cur.fl & kSolid))) {
             const long long own = gx + (long long)g.nx * (gy + (long long)g.ny * z_prev);
-            const float2* rm = ring + ((e - 2) & 3) * RH * RW + own_off;
             const float2* rc = ring + ((e - 1) & 3) * RH * RW + own_off;
-            const float2* rp = ring + slot * RH * RW + own_off;
             float dA, dB, j[3];
             if constexpr (!packed) {
                 sums(cur.d, dA, dB, j);
@@ -426,12 +435,18 @@ fused_box_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t*
                 for (int a = 0; a < 3; ++a) j[a] = cur.j[a];
             }
             float SA[3], SB[3];
-            neighbour_sums(
-                [&](int dx, int dy, int dz) {
-                    const float2* r = dz < 0 ? rm : (dz > 0 ? rp : rc);
-                    return r[dy * RW + dx];
-                },
-                SA, SB);
+            if constexpr (packed) {
+                force_sums(ps_lo, ps_mid, ps_hi, rc[RW + 1], rc[RW - 1], rc[1 - RW], rc[-1 - RW], SA, SB);
+            } else {
+                const float2* rm = ring + ((e - 2) & 3) * RH * RW + own_off;
+                const float2* rp = ring + slot * RH * RW + own_off;
+                neighbour_sums<kFactoredSums<S>>(
+                    [&](int dx, int dy, int dz) {
+                        const float2* r = dz < 0 ? rm : (dz > 0 ? rp : rc);
+                        return r[dy * RW + dx];
+                    },
+                    SA, SB);
+            }
             const bool solid = MASK && (cur.fl & kSolid);
             if (mom_out != nullptr && !solid) store_moments(mom_out, g, own, dA, dB, j, SA, SB);
             if constexpr (packed)
@@ -443,6 +458,10 @@ fused_box_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t*
                     p, dA, dB, j, SA, SB, dst, g, (int)own, solid);
             else
                 collide_store<S, MASK>(cur.d, p, dA, dB, j, SA, SB, dst, g, (int)own, solid);
+        }
+        if constexpr (packed) {
+            ps_lo = ps_mid;
+            ps_mid = ps_hi;
         }
         z_prev = z_cur;
         z_cur = wrap_inc(z_cur, g.nz);

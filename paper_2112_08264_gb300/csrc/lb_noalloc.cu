@@ -109,7 +109,7 @@ __global__ void moments_from_f_kernel(const float* __restrict__ f, const uint8_t
     if (oB) oB[s] = rB;
     if (!ou) return;
     float SA[3], SB[3];
-    neighbour_sums(
+    neighbour_sums<false>(
         [&](int dx, int dy, int dz) {
             const int xx = dx > 0 ? wrap_inc(x, g.nx) : (dx < 0 ? wrap_dec(x, g.nx) : x);
             const int yy = dy > 0 ? wrap_inc(y, g.ny) : (dy < 0 ? wrap_dec(y, g.ny) : y);

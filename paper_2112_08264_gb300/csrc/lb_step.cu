@@ -108,7 +108,7 @@ fused_step_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t
             float dA, dB, j[3];
             sums(cur, dA, dB, j);
             float SA[3], SB[3];
-            neighbour_sums(
+            neighbour_sums<kFactoredSums<S>>(
                 [&](int dx, int dy, int dz) {
                     const int s = dz < 0 ? slot_m : (dz > 0 ? slot_p : slot_c);
                     return ring[s][ty + 1 + dy][tx + 1 + dx];
@@ -163,7 +163,7 @@ collide_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t* _
     float dA, dB, j[3];
     sums(d, dA, dB, j);
     float SA[3], SB[3];
-    neighbour_sums(
+    neighbour_sums<kFactoredSums<S>>(
         [&](int dx, int dy, int dz) {
             const int xx = dx > 0 ? wrap_inc(x, g.nx) : (dx < 0 ? wrap_dec(x, g.nx) : x);
             const int yy = dy > 0 ? wrap_inc(y, g.ny) : (dy < 0 ? wrap_dec(y, g.ny) : y);
