@@ -90,9 +90,10 @@ void lb_default_options(lb_options* opt);
 
 /* Bytes of device workspace lb_create needs for this grid and options
  * (two population buffers, density scratch, reduction scratch, the solid
- * flags when a mask is used -- counted always -- and, when
- * opt->ckpt_every > 0, checkpoints plus the adjoint's buffers). opt may be
- * NULL (defaults). Returns 0 for invalid sizes. Pure host function. */
+ * flags and the bounce-back link list (up to N links) when a mask is used --
+ * counted always -- and, when opt->ckpt_every > 0, checkpoints plus the
+ * adjoint's buffers). opt may be NULL (defaults). Returns 0 for invalid
+ * sizes. Pure host function. */
 size_t lb_workspace_bytes(int nx, int ny, int nz, const lb_options* opt);
 
 /* Create a context over the caller's workspace.
@@ -105,7 +106,8 @@ size_t lb_workspace_bytes(int nx, int ny, int nz, const lb_options* opt);
  *   d_workspace device pointer, 256-byte aligned, ws_bytes >= lb_workspace_bytes.
  *   stream      a cudaStream_t (NULL = the legacy default stream).
  * Errors: LB_EINVAL for bad sizes/parameters/alignment, LB_ENOMEM for a short
- * workspace, LB_ECUDA. Synchronous (the mask upload waits). */
+ * workspace, LB_ECUDA. Synchronous (the mask upload and the construction of
+ * its link list -- the fluid sites next to a solid one, per velocity -- wait). */
 lb_status lb_create(int nx, int ny, int nz, float tau, float G, const uint8_t* mask,
                     const lb_options* opt, void* d_workspace, size_t ws_bytes,
                     void* stream, lb_ctx** out);

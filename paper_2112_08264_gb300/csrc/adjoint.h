@@ -50,6 +50,7 @@ struct AdjointRun {
     int zsplit;
     AsyncPlan plan;         // forward (recompute) plan
     AsyncPlan adjplan;      // fused box adjoint plan; adjplan.box == 0: two-pass adjoint
+    LinkList links;         // bounce-back links of the mask (recompute)
 };
 
 size_t adjoint_workspace_bytes(int nx, int ny, int nz, int K);

@@ -24,6 +24,15 @@ struct AsyncPlan {
 };
 
 // One time step: src (post-collision state) -> dst.
+// Bounce-back links of a static mask: for each velocity i, the fluid sites x
+// whose neighbour x + c_i is solid, in segment [off[i], off[i + 1]) of
+// `sites` (grouped by blocks of 256 consecutive sites, ascending within a
+// warp). sites == nullptr: no list (the copy pass scans every site).
+struct LinkList {
+    const uint32_t* sites = nullptr;
+    long long off[Q + 1] = {};
+};
+
 struct StepLaunch {
     int prec;                 // 0 fp32, 1 fp16 deviation, 2 bf16 deviation
     int kernel;               // 0 fused (async copies), 1 two-pass, 2 fused (register double buffer)
@@ -36,6 +45,7 @@ struct StepLaunch {
     Phys p;
     int zsplit;               // register fused kernel: z-chunks per tile column
     AsyncPlan plan;           // async fused kernel
+    LinkList links;           // masked grids: the write-side bounce-back links
 };
 
 cudaError_t launch_step(const StepLaunch& L, cudaStream_t st);
@@ -50,11 +60,18 @@ cudaError_t launch_fused_async(const StepLaunch& L, cudaStream_t st);
 // Solid flags from a device mask (1 = solid).
 cudaError_t launch_flags(const uint8_t* mask, uint32_t* flags, const Geom& g, cudaStream_t st);
 
+// Build the link list of a mask (flags) into `sites` (capacity entries) with
+// `cursor` (2Q device words of scratch); the host waits for the counts. On
+// return L.sites is set when the links fit, else left nullptr.
+cudaError_t build_links(const uint32_t* flags, uint32_t* sites, size_t capacity, uint32_t* cursor, const Geom& g,
+                        LinkList& L, cudaStream_t st);
+
 // Write-side halfway bounce-back on a freshly written state g: for every fluid
 // node x and direction i with x + c_i solid, copy g_i(x) into slot opp(i) of
 // x + c_i. The next pull of population opp(i) at x, from x - c_opp(i) = x + c_i,
 // then reads the bounced value without a mask test. Run after every masked step.
-cudaError_t launch_reflect(int prec, void* g_state, const uint32_t* flags, const Geom& g, cudaStream_t st);
+cudaError_t launch_reflect(int prec, void* g_state, const uint32_t* flags, const LinkList& links, const Geom& g,
+                           cudaStream_t st);
 
 // Internal state from a post-streaming population field: either the
 // equilibrium of (rhoA, rhoB, u) (f == nullptr) or the given f (float,

@@ -39,7 +39,7 @@ namespace {
 size_t store_bytes(int prec) { return prec == LB_FP32 ? 4 : 2; }
 
 struct Layout {
-    size_t pop[2], mask, flags, rho, red_part, red_out;
+    size_t pop[2], mask, flags, links, cursor, rho, red_part, red_out;
     size_t ckpt, ckpt_slots, seg, adj;
     size_t state_bytes;
     size_t total;
@@ -71,6 +71,8 @@ Layout make_layout(int nx, int ny, int nz, const lb_options& o) {
     L.pop[1] = off; off += L.state_bytes;
     L.mask = off; off += align256(N);
     L.flags = off; off += align256(N * 4);
+    L.links = off; off += align256(N * 4);   // bounce-back link list (masked grids), up to N links
+    L.cursor = off; off += align256(2 * Q * 4);
     L.rho = off; off += align256(2 * N * 4);
     L.red_part = off; off += align256((size_t)kRedBlocks * kRedVals * 8);
     L.red_out = off; off += align256(kRedVals * 8);
@@ -107,6 +109,7 @@ struct lb_ctx {
     int sm_count, tiles, zsplit, threads;
     AsyncPlan plan;
     AsyncPlan adjplan;
+    LinkList links;     // write-side bounce-back links of the mask
     // recording for the adjoint
     bool recording;       // lb_init was called with ckpt_every > 0 and the run is intact
     double rho0_d[2];
@@ -217,6 +220,9 @@ lb_status lb_create(int nx, int ny, int nz, float tau, float G, const uint8_t* m
     if (mask) {
         e = cudaMemcpyAsync(c->mask_dev, mask, (size_t)c->g.N, cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess) e = launch_flags(c->mask_dev, c->flags, c->g, c->stream);
+        if (e == cudaSuccess)
+            e = build_links(c->flags, reinterpret_cast<uint32_t*>(c->ws + L.links), (size_t)c->g.N,
+                            reinterpret_cast<uint32_t*>(c->ws + L.cursor), c->g, c->links, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) {
             delete c;
@@ -272,6 +278,7 @@ lb_status lb_step(lb_ctx* c, int n) {
     S.p = c->p;
     S.zsplit = c->zsplit;
     S.plan = c->plan;
+    S.links = c->links;
     for (int t = 0; t < n; ++t) {
         S.src = c->pop[c->cur];
         S.dst = c->pop[1 - c->cur];
@@ -348,6 +355,7 @@ lb_status lb_backward(lb_ctx* c, const float* dLA, const float* dLB, float* gA, 
     R.zsplit = c->zsplit;
     R.plan = c->plan;
     R.adjplan = c->adjplan;
+    R.links = c->links;
     R.kernel = c->opt.kernel;
     double gG_host = 0.0;
     cudaError_t e = run_adjoint(R, dLA, dLB, gA, gB, &gG_host, c->stream);

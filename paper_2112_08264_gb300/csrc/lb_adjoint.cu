@@ -566,6 +566,7 @@ cudaError_t run_adjoint(const AdjointRun& R, const float* dLA, const float* dLB,
     S.p = R.p;
     S.zsplit = R.zsplit;
     S.plan = R.plan;
+    S.links = R.links;
     const AsyncPlan& AP = R.adjplan;
     const int adj_blocks = AP.ncols * AP.R * AP.zsplit;
     for (long long m = M - 1; m >= 0; --m) {

@@ -1,6 +1,7 @@
 // lb_aux.cu -- kernels around the time step: solid flags, initial state
 // (equilibrium, Eq. LEQ) and state import/export, moments, and the FP64
 // conservation reduction.
+#include <algorithm>
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -59,6 +60,79 @@ __global__ void reflect_kernel(const S* __restrict__ in, S* __restrict__ out,
             const long long t = nb_index<i>(g, x, y, z);
             *reinterpret_cast<P*>(out + pidx(0, o, (uint32_t)t)) = v[i];
         }
+    });
+}
+
+// Link list, pass 1: per velocity, the number of fluid sites x with x + c_i
+// solid (flag bit opp(i)); block totals in shared memory, one global atomic
+// per velocity and block.
+__global__ void link_count_kernel(const uint32_t* __restrict__ flags, uint32_t* __restrict__ counts, Geom g) {
+    __shared__ uint32_t cnt[Q];
+    if (threadIdx.x < Q) cnt[threadIdx.x] = 0u;
+    __syncthreads();
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t fl = s < g.N ? __ldg(flags + s) : kSolid;
+    const bool fluid = !(fl & kSolid);
+    static_for<1, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        const unsigned b = __ballot_sync(0xffffffffu, fluid && (fl & (1u << Vel<i>::opp)));
+        if ((threadIdx.x & 31) == 0 && b) atomicAdd(&cnt[i], (uint32_t)__popc(b));
+    });
+    __syncthreads();
+    if (threadIdx.x >= 1 && threadIdx.x < Q && cnt[threadIdx.x]) atomicAdd(&counts[threadIdx.x], cnt[threadIdx.x]);
+}
+
+// Link list, pass 2: each block reserves its share of every velocity's
+// segment with one atomic, warps take consecutive parts of it, lanes their
+// rank within the warp.
+__global__ void link_fill_kernel(const uint32_t* __restrict__ flags, uint32_t* __restrict__ cursor,
+                                 uint32_t* __restrict__ sites, LinkList L, Geom g) {
+    __shared__ uint32_t cnt[Q], base[Q];
+    if (threadIdx.x < Q) cnt[threadIdx.x] = 0u;
+    __syncthreads();
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t fl = s < g.N ? __ldg(flags + s) : kSolid;
+    const bool fluid = !(fl & kSolid);
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t wpos[Q];
+    static_for<1, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        const unsigned b = __ballot_sync(0xffffffffu, fluid && (fl & (1u << Vel<i>::opp)));
+        uint32_t w = 0u;
+        if (lane == 0 && b) w = atomicAdd(&cnt[i], (uint32_t)__popc(b));
+        wpos[i] = __shfl_sync(0xffffffffu, w, 0) + (uint32_t)__popc(b & lt);
+    });
+    __syncthreads();
+    if (threadIdx.x >= 1 && threadIdx.x < Q)
+        base[threadIdx.x] = cnt[threadIdx.x] ? atomicAdd(&cursor[threadIdx.x], cnt[threadIdx.x]) : 0u;
+    __syncthreads();
+    static_for<1, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        if (fluid && (fl & (1u << Vel<i>::opp))) sites[L.off[i] + base[i] + wpos[i]] = (uint32_t)s;
+    });
+}
+
+// The copy pass over the links: block row blockIdx.y + 1 = velocity i; one
+// pair copy per link, g_i(x) into slot opp(i) of x + c_i.
+template <typename S>
+__global__ void reflect_links_kernel(const S* __restrict__ in, S* __restrict__ out, LinkList L, Geom g) {
+    using P = typename Store<S>::Pair;
+    const int vel = (int)blockIdx.y + 1;
+    static_for<1, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        if (vel != i) return;
+        const long long k = L.off[i] + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+        if (k >= L.off[i + 1]) return;
+        const uint32_t x0 = __ldg(L.sites + k);
+        int x, y, z;
+        site_xyz(x0, g, x, y, z);
+        const P v = __ldg(reinterpret_cast<const P*>(in + pidx(0, i, x0)));
+        x = Vel<i>::x > 0 ? wrap_inc(x, g.nx) : (Vel<i>::x < 0 ? wrap_dec(x, g.nx) : x);
+        y = Vel<i>::y > 0 ? wrap_inc(y, g.ny) : (Vel<i>::y < 0 ? wrap_dec(y, g.ny) : y);
+        z = Vel<i>::z > 0 ? wrap_inc(z, g.nz) : (Vel<i>::z < 0 ? wrap_dec(z, g.nz) : z);
+        const uint32_t t = (uint32_t)x + (uint32_t)g.nx * ((uint32_t)y + (uint32_t)g.ny * (uint32_t)z);
+        *reinterpret_cast<P*>(out + pidx(0, Vel<i>::opp, t)) = v;
     });
 }
 
@@ -281,7 +355,41 @@ cudaError_t launch_flags(const uint8_t* mask, uint32_t* flags, const Geom& g, cu
     return cudaGetLastError();
 }
 
-cudaError_t launch_reflect(int prec, void* g_state, const uint32_t* flags, const Geom& g, cudaStream_t st) {
+cudaError_t build_links(const uint32_t* flags, uint32_t* sites, size_t capacity, uint32_t* cursor, const Geom& g,
+                        LinkList& L, cudaStream_t st) {
+    L = LinkList{};
+    const unsigned nb = blocks_for(g.N, 256);
+    cudaError_t e = cudaMemsetAsync(cursor, 0, 2 * Q * sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    link_count_kernel<<<nb, 256, 0, st>>>(flags, cursor, g);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    uint32_t counts[Q];
+    if ((e = cudaMemcpyAsync(counts, cursor, Q * sizeof(uint32_t), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return e;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+    LinkList T;
+    T.off[0] = T.off[1] = 0;
+    for (int i = 1; i < Q; ++i) T.off[i + 1] = T.off[i] + counts[i];
+    if ((size_t)T.off[Q] > capacity) return cudaSuccess;   // too many links: the pass scans every site
+    T.sites = sites;
+    if ((e = cudaMemsetAsync(cursor + Q, 0, Q * sizeof(uint32_t), st)) != cudaSuccess) return e;
+    link_fill_kernel<<<nb, 256, 0, st>>>(flags, cursor + Q, sites, T, g);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    L = T;
+    return cudaStreamSynchronize(st);
+}
+
+cudaError_t launch_reflect(int prec, void* g_state, const uint32_t* flags, const LinkList& links, const Geom& g,
+                           cudaStream_t st) {
+    if (links.sites) {
+        long long most = 0;
+        for (int i = 1; i < Q; ++i) most = std::max(most, links.off[i + 1] - links.off[i]);
+        if (most == 0) return cudaSuccess;
+        const dim3 grid((unsigned)((most + 255) / 256), Q - 1, 1);
+#define LBGB_REFLECT(T) [&] { reflect_links_kernel<T><<<grid, 256, 0, st>>>((const T*)g_state, (T*)g_state, links, g); }
+        return by_prec(prec, LBGB_REFLECT(float), LBGB_REFLECT(__half), LBGB_REFLECT(__nv_bfloat16));
+#undef LBGB_REFLECT
+    }
     const unsigned nb = blocks_for(g.N, 256);
 #define LBGB_REFLECT(T) [&] { reflect_kernel<T><<<nb, 256, 0, st>>>((const T*)g_state, (T*)g_state, flags, g); }
     return by_prec(prec, LBGB_REFLECT(float), LBGB_REFLECT(__half), LBGB_REFLECT(__nv_bfloat16));

@@ -212,7 +212,7 @@ cudaError_t launch_step_kernels(const StepLaunch& L, cudaStream_t st) {
 cudaError_t launch_step(const StepLaunch& L, cudaStream_t st) {
     const cudaError_t e = launch_step_kernels(L, st);
     if (e != cudaSuccess || L.flags == nullptr) return e;
-    return launch_reflect(L.prec, L.dst, L.flags, L.g, st);
+    return launch_reflect(L.prec, L.dst, L.flags, L.links, L.g, st);
 }
 
 void fused_geometry(int nx, int ny, int nz, int sm_count, int* tiles, int* zsplit, int* threads) {
