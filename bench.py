@@ -163,6 +163,11 @@ def workload(name, grid=None):
         mask, _ = inputs.colloid_mask(n, n, n, n_spheres=4000, radius=5.0, seed=4321)
         return dict(shape=(n, n, n), tau=1.0, G=0.65, rA=rA, rB=rB, mask=mask,
                     desc="256^3, 4000 static spheres R=5 (seed 4321), halfway bounce-back")
+    if name == "orderparam256":
+        n = grid or 256
+        rA, rB = inputs.random_order_parameter(n, n, n, seed=1234)
+        return dict(shape=(n, n, n), tau=1.0, G=0.65, rA=rA, rB=rB, mask=None,
+                    desc="%d^3 periodic, random order parameter +-0.9 per site (seed 1234), tau=1, G=0.65" % n)
     if name == "spinodal512":
         n = 512
         rA, rB = inputs.spinodal(n, n, n, seed=1234)
@@ -332,7 +337,8 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="spinodal256", choices=["spinodal256", "colloid256", "spinodal512"])
+    ap.add_argument("--config", default="spinodal256",
+                    choices=["spinodal256", "colloid256", "orderparam256", "spinodal512"])
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--kernel", default="fused", choices=["fused", "two_pass"])
     ap.add_argument("--grid", type=int, default=None, help="override the spinodal grid size (profiling)")
@@ -396,6 +402,7 @@ def main():
                                % info["launches_per_step"]),
                      "traffic": (tps * N if tps is not None else None)},
         "gpu_launches": args.steps * info["launches_per_step"],
+        "fluid_glups": glups * fluid,   # fluid site updates only (all sites count in value)
         "clocks": clocks,
         "conserved_totals": [float(x) for x in st],
     }
