@@ -74,6 +74,15 @@ typedef enum { LB_FP32 = 0, LB_FP16_DEV = 1, LB_BF16_DEV = 2 } lb_precision;
  * results bit for bit). */
 typedef enum { LB_KERNEL_FUSED = 0, LB_KERNEL_TWO_PASS = 1, LB_KERNEL_FUSED_REG = 2 } lb_kernel;
 
+/* Two-component model. SHAN_CHEN: BGK with the Shan-Chen pseudopotential
+ * force and the velocity shift (tau and G of lb_create). COLOUR_GRADIENT:
+ * the paper's colour-gradient model (Appendix, Eq. 1coll, 2coll, 3coll): BGK
+ * at the mixture viscosity, the perturbation that builds the interfacial
+ * tension sigma, and the recolouring with parameter beta; periodic grids only
+ * (no mask, no body force, no recording for lb_backward); lb_create's tau
+ * and G are not used (pass tau > 0.5). */
+typedef enum { LB_MODEL_SHAN_CHEN = 0, LB_MODEL_COLOUR_GRADIENT = 1 } lb_model;
+
 typedef struct {
     int prec;              /* lb_precision (default LB_FP32) */
     int kernel;            /* lb_kernel (default LB_KERNEL_FUSED) */
@@ -83,6 +92,12 @@ typedef struct {
     int ckpt_every;        /* K > 0: lb_step records a checkpoint every K steps
                               for lb_backward; 0 = no recording (default) */
     int ckpt_steps_max;    /* longest recorded run, in steps (needed when K > 0) */
+    int model;             /* lb_model (default LB_MODEL_SHAN_CHEN) */
+    double cg_nu_A, cg_nu_B; /* colour gradient: kinematic viscosities of the pure
+                              components, > 0 (omega = 2 / (6 nu_bar + 1) with
+                              1/nu_bar = (rho^A/rho)/nu_A + (rho^B/rho)/nu_B) */
+    double cg_sigma;       /* colour gradient: surface tension, >= 0 (A = 9 omega sigma / 4) */
+    double cg_beta;        /* colour gradient: recolouring parameter, in [0, 1] */
 } lb_options;
 
 /* Fill *opt with the defaults above. */
@@ -119,7 +134,8 @@ lb_status lb_set_stream(lb_ctx* ctx, void* stream);
  * device fields d_rhoA, d_rhoB (N floats) and d_u (3N floats SoA, or NULL
  * for u = 0). Resets the step counter and any recording. LB_EINVAL if a
  * fluid node has rho^k <= 0 or a non-finite input (the force shift divides
- * by rho^k). Synchronous. */
+ * by rho^k); with the colour-gradient model pure phases are allowed
+ * (rho^k >= 0, rho^A + rho^B > 0). Synchronous. */
 lb_status lb_init(lb_ctx* ctx, const float* d_rhoA, const float* d_rhoB, const float* d_u);
 
 /* Advance n >= 1 time steps (Eq. bgk with the force shift, then streaming

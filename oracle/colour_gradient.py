@@ -24,8 +24,10 @@ sub-step, on periodic grids without solid nodes:
                  velocity or a vanishing gradient               (Eq. 3coll)
   streaming      f_i^k(x + c_i, t + 1) = f^k_i(x)               (Eq. CGLBE)
 
-The perturbation and recolouring act only where grad Theta != 0 (0/0 is
-taken as 0). Populations are ``(2, 19, nz, ny, nx)`` in the velocity order of
+The perturbation and recolouring act only where |grad Theta| > GRAD_MIN =
+1e-5 (the paper does not say how a vanishing gradient is treated; cos(phi_i)
+has no limit there, and a gradient at the rounding level of a float32 state
+has no meaningful direction). Populations are ``(2, 19, nz, ny, nx)`` in the velocity order of
 ``lb_numpy`` (``to_public`` / ``from_public`` map to the library's order).
 """
 import numpy as np
@@ -34,6 +36,7 @@ from .lb_numpy import CS2, VEL, W, equilibrium, shift_from, shift_to
 
 # B_i of the Appendix coefficient table, by |c|^2 = 0, 1, 2
 _B_BY_C2 = {0: -2.0 / 9.0, 1: 1.0 / 54.0, 2: 1.0 / 27.0}
+GRAD_MIN = 1e-5
 B = np.array([_B_BY_C2[int((c * c).sum())] for c in VEL])
 CNORM = np.sqrt((VEL * VEL).sum(axis=1).astype(np.float64))
 
@@ -63,7 +66,7 @@ def perturbation(A, grad):
     """(Omega_i^k)^(2) of Eq. 2coll for one component: shape (19, ...)."""
     g2 = (grad * grad).sum(axis=0)
     gn = np.sqrt(g2)
-    nz = g2 > 0
+    nz = gn > GRAD_MIN
     out = []
     for i, c in enumerate(VEL):
         cg = c[0] * grad[0] + c[1] * grad[1] + c[2] * grad[2]
@@ -75,7 +78,7 @@ def perturbation(A, grad):
 def cos_phi(grad):
     """cos of the angle between c_i and grad Theta: shape (19, ...)."""
     gn = np.sqrt((grad * grad).sum(axis=0))
-    nz = gn > 0
+    nz = gn > GRAD_MIN
     out = []
     for i, c in enumerate(VEL):
         if not c.any():

@@ -11,6 +11,7 @@ from . import build as _build
 LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_ENONFINITE, LB_ESTATE, LB_ETIMEOUT = range(7)
 PRECISIONS = {"fp32": 0, "fp16": 1, "bf16": 2}
 KERNELS = {"fused": 0, "two_pass": 1, "fused_reg": 2}
+MODELS = {"shan_chen": 0, "colour_gradient": 1}
 
 
 class LbOptions(ctypes.Structure):
@@ -22,6 +23,11 @@ class LbOptions(ctypes.Structure):
         ("body_force", ctypes.c_double * 3),
         ("ckpt_every", ctypes.c_int),
         ("ckpt_steps_max", ctypes.c_int),
+        ("model", ctypes.c_int),
+        ("cg_nu_A", ctypes.c_double),
+        ("cg_nu_B", ctypes.c_double),
+        ("cg_sigma", ctypes.c_double),
+        ("cg_beta", ctypes.c_double),
     ]
 
 
@@ -92,9 +98,16 @@ def check(status, what):
 
 
 def options(prec="fp32", kernel="fused", rho0=(0.0, 0.0), body_force=(0.0, 0.0, 0.0),
-            ckpt_every=0, ckpt_steps_max=0):
+            ckpt_every=0, ckpt_steps_max=0, model="shan_chen", cg=None):
+    """lb_options; ``cg`` = dict(nu=(nu_A, nu_B), sigma=, beta=) for the
+    colour-gradient model."""
     o = LbOptions()
     lib().lb_default_options(ctypes.byref(o))
+    o.model = MODELS[model] if isinstance(model, str) else int(model)
+    if cg is not None:
+        o.cg_nu_A, o.cg_nu_B = float(cg["nu"][0]), float(cg["nu"][1])
+        o.cg_sigma = float(cg.get("sigma", 0.0))
+        o.cg_beta = float(cg.get("beta", 0.0))
     o.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
     o.kernel = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
     o.rho0_A, o.rho0_B = float(rho0[0]), float(rho0[1])

@@ -52,6 +52,10 @@ struct Phys {
     float G;         // Shan-Chen coupling
     float g[3];      // body force
     float rho0[2];   // deviation base of components A, B
+    int model;       // 0 Shan-Chen, 1 colour gradient
+    float cg_inu[2]; // colour gradient: 1 / nu of the pure components
+    float cg_sigma;  // colour gradient: surface tension
+    float cg_beta;   // colour gradient: recolouring parameter
 };
 
 // solid-site flags: bit 0 = this node is solid; bit i (1..18) = node x - c_i
@@ -208,6 +212,61 @@ __device__ __forceinline__ void collide_store(const float (&d)[2][Q], const Phys
                                               const float (&SB)[3], S* __restrict__ dst,
                                               const Geom& g, int own, bool zero = false) {
     collide_store_g<S, Z>([&](int k, int i) { return d[k][i]; }, p, dA, dB, j, SA, SB, dst, g, own, zero);
+}
+
+// Colour-gradient collision (Appendix: Eq. 1coll, BGK at the mixture
+// viscosity; Eq. 2coll, the perturbation with A = 9 omega sigma / 4 and the
+// table's B_i; Eq. 3coll, the recolouring) in deviation form, and store of the
+// post-collision node. gt = grad Theta, Theta = (rho^A - rho^B) / rho. With
+// f*_i = f_i^A,(2) + f_i^B,(2) = w_i (rho0^A + rho0^B) + D_i, the recoloured
+// deviations are
+//   d_i^A =  w_i e + (rho^A / rho) D_i + X_i,   d_i^B = -w_i e + (rho^B / rho) D_i - X_i,
+// e = (rho^A rho0^B - rho0^A rho^B) / rho, X_i = beta (rho^A rho^B / rho) w_i cos(phi_i),
+// which conserves the mass of each component and the total momentum.
+template <typename S, typename DGet>
+__device__ __forceinline__ void cg_collide_store_g(DGet&& dget, const Phys& p, float dA, float dB,
+                                                   const float (&j)[3], const float (&gt)[3],
+                                                   S* __restrict__ dst, int own) {
+    const float rA = p.rho0[0] + dA, rB = p.rho0[1] + dB;
+    const float inv = __fdividef(1.0f, rA + rB);
+    const float u[3] = {j[0] * inv, j[1] * inv, j[2] * inv};
+    const float uu15 = 1.5f * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    const float inu = (rA * p.cg_inu[0] + rB * p.cg_inu[1]) * inv;   // 1 / nu_bar
+    const float omega = __fdividef(2.0f * inu, 6.0f + inu);           // 2 / (6 nu_bar + 1)
+    const float om1 = 1.0f - omega;
+    const float g2 = gt[0] * gt[0] + gt[1] * gt[1] + gt[2] * gt[2];
+    // 1 / |grad Theta|; 0 (no perturbation, no recolouring) where |grad Theta|
+    // <= 1e-5: the direction of a gradient at the rounding level of the state
+    // is undefined, and cos(phi_i) has no limit at grad Theta = 0
+    const float q = g2 > 1e-10f ? rsqrtf(g2) : 0.f;
+    const float gn = g2 * q;                           // |grad Theta|
+    const float hA = 1.125f * omega * p.cg_sigma;     // A / 2
+    const float kc = p.cg_beta * rA * rB * inv * q;   // beta rho^A rho^B / (rho |grad Theta|)
+    const float e = (rA * p.rho0[1] - p.rho0[0] * rB) * inv;
+    const float fa = rA * inv, fb = rB * inv;
+    S* out = dst + blk_base((uint32_t)own);
+    static_for<0, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        float cu = 0.f, cg = 0.f;
+        if constexpr (Vel<i>::x != 0) { cu += Vel<i>::x * u[0]; cg += Vel<i>::x * gt[0]; }
+        if constexpr (Vel<i>::y != 0) { cu += Vel<i>::y * u[1]; cg += Vel<i>::y * gt[1]; }
+        if constexpr (Vel<i>::z != 0) { cu += Vel<i>::z * u[2]; cg += Vel<i>::z * gt[2]; }
+        constexpr float w = wgt<i>();
+        constexpr float Bi = Vel<i>::c2 == 0 ? -2.0f / 9.0f : (Vel<i>::c2 == 1 ? 1.0f / 54.0f : 1.0f / 27.0f);
+        constexpr float wrc = Vel<i>::c2 == 2 ? w * 0.70710678f : w;   // w_i / |c_i| (cg = 0 at rest)
+        const float poly = cu * (3.0f + 4.5f * cu) - uu15;
+        const float pert = hA * (w * cg * cg * q - Bi * gn);
+        const float d2A = om1 * dget(0, i) + omega * w * (dA + rA * poly) + pert;
+        const float d2B = om1 * dget(1, i) + omega * w * (dB + rB * poly) + pert;
+        const float D = d2A + d2B;
+        const float X = kc * wrc * cg;
+        Store<S>::st2(out + i * (2 * kBlk), w * e + fa * D + X, -w * e + fb * D - X);
+    });
+}
+
+// Phase field Theta = (rho^A - rho^B) / rho from the density deviations.
+__device__ __forceinline__ float phase_field(const Phys& p, float dA, float dB) {
+    return __fdividef((p.rho0[0] - p.rho0[1]) + (dA - dB), (p.rho0[0] + p.rho0[1]) + (dA + dB));
 }
 
 // Per-node moments kept by the adjoint's recompute, 11 fields: drho^A,

@@ -98,9 +98,11 @@ cudaError_t launch_stats(int prec, const void* src, const uint32_t* flags, doubl
                          const Geom& g, const Phys& p, cudaStream_t st);
 
 // Checks of lb_init inputs over fluid nodes: out = {sum rhoA, sum rhoB,
-// fluid count, bad count (rho <= 0 or not finite), 0, 0}.
+// fluid count, bad count, 0, 0}. Bad: not finite, or rho^k <= 0 (Shan-Chen
+// divides by each rho^k), or, with allow_zero (colour gradient, which
+// divides only by rho^A + rho^B), rho^k < 0 or rho^A + rho^B <= 0.
 cudaError_t launch_check_init(const float* rhoA, const float* rhoB, const float* u, const uint32_t* flags,
-                              double* partials, double* out, const Geom& g, cudaStream_t st);
+                              double* partials, double* out, const Geom& g, bool allow_zero, cudaStream_t st);
 
 // Message returned by lb_last_error() (host code only).
 void record_error_text(const char* msg);

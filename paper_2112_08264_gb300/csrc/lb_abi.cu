@@ -59,6 +59,16 @@ bool valid_options(const lb_options& o) {
         if (!std::isfinite(g)) return false;
     if (o.ckpt_every < 0 || o.ckpt_steps_max < 0) return false;
     if (o.ckpt_every > 0 && o.ckpt_steps_max < 1) return false;
+    if (o.model != LB_MODEL_SHAN_CHEN && o.model != LB_MODEL_COLOUR_GRADIENT) return false;
+    if (o.model == LB_MODEL_COLOUR_GRADIENT) {
+        if (!(std::isfinite(o.cg_nu_A) && o.cg_nu_A > 0.0 && std::isfinite(o.cg_nu_B) && o.cg_nu_B > 0.0))
+            return false;
+        if (!(std::isfinite(o.cg_sigma) && o.cg_sigma >= 0.0)) return false;
+        if (!(std::isfinite(o.cg_beta) && o.cg_beta >= 0.0 && o.cg_beta <= 1.0)) return false;
+        for (double g : o.body_force)
+            if (g != 0.0) return false;
+        if (o.ckpt_every != 0 || o.kernel == LB_KERNEL_FUSED_REG) return false;
+    }
     return true;
 }
 
@@ -124,6 +134,13 @@ Phys make_phys(float tau, float G, const lb_options& o) {
     p.G = G;
     for (int a = 0; a < 3; ++a) p.g[a] = (float)o.body_force[a];
     p.rho0[0] = p.rho0[1] = 1.0f;
+    p.model = o.model;
+    if (o.model == LB_MODEL_COLOUR_GRADIENT) {
+        p.cg_inu[0] = (float)(1.0 / o.cg_nu_A);
+        p.cg_inu[1] = (float)(1.0 / o.cg_nu_B);
+        p.cg_sigma = (float)o.cg_sigma;
+        p.cg_beta = (float)o.cg_beta;
+    }
     return p;
 }
 
@@ -138,7 +155,8 @@ lb_status run_reduction(lb_ctx* c, double out[kRedVals], bool stats, const float
     cudaError_t e = stats ? launch_stats(c->opt.prec, c->pop[c->cur], c->has_mask ? c->flags : nullptr,
                                          c->red_part, c->red_out, c->g, c->p, c->stream)
                           : launch_check_init(rA, rB, u, c->has_mask ? c->flags : nullptr, c->red_part,
-                                              c->red_out, c->g, c->stream);
+                                              c->red_out, c->g, c->opt.model == LB_MODEL_COLOUR_GRADIENT,
+                                              c->stream);
     if (e != cudaSuccess) return cuda_status("reduction launch", e);
     e = cudaMemcpyAsync(out, c->red_out, kRedVals * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     if (e != cudaSuccess) return cuda_status("reduction copy", e);
@@ -175,6 +193,7 @@ lb_status lb_create(int nx, int ny, int nz, float tau, float G, const uint8_t* m
     if (opt) o = *opt;
     if (!valid_dims(nx, ny, nz) || !valid_options(o)) return LB_EINVAL;
     if (!std::isfinite(tau) || !(tau > 0.5f) || !std::isfinite(G)) return LB_EINVAL;
+    if (o.model == LB_MODEL_COLOUR_GRADIENT && mask) return LB_EINVAL;   // periodic grids only
     if (!d_workspace || ((uintptr_t)d_workspace & 255u)) return LB_EINVAL;
     const Layout L = make_layout(nx, ny, nz, o);
     if (ws_bytes < L.total) return LB_ENOMEM;

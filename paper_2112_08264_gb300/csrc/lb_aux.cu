@@ -256,6 +256,12 @@ __global__ void moments_kernel(const S* __restrict__ src, const uint32_t* __rest
     if (oA) oA[s] = rA;
     if (oB) oB[s] = rB;
     if (!ou) return;
+    if (p.model == 1) {   // colour gradient: no body force, u = j / rho
+        const float inv = 1.0f / (rA + rB);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) ou[a * g.N + s] = j[a] * inv;
+        return;
+    }
     float SA[3], SB[3];
     neighbour_sums<kFactoredSums<S>>(
         [&](int dx, int dy, int dz) {
@@ -309,13 +315,14 @@ stats_kernel(const S* __restrict__ src, const uint32_t* __restrict__ flags, doub
 
 __global__ void check_init_kernel(const float* __restrict__ rA, const float* __restrict__ rB,
                                   const float* __restrict__ u, const uint32_t* __restrict__ flags,
-                                  double* __restrict__ partials, Geom g) {
+                                  double* __restrict__ partials, Geom g, bool allow_zero) {
     double v[kRedVals] = {0, 0, 0, 0, 0, 0};
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.N; s += stride) {
         if (flags && (flags[s] & kSolid)) continue;
         const float a = rA[s], b = rB[s];
-        bool ok = (a > 0.f) && (b > 0.f) && isfinite(a) && isfinite(b);
+        bool ok = isfinite(a) && isfinite(b) &&
+                  (allow_zero ? (a >= 0.f && b >= 0.f && a + b > 0.f) : (a > 0.f && b > 0.f));
         if (u) ok = ok && isfinite(u[s]) && isfinite(u[g.N + s]) && isfinite(u[2 * g.N + s]);
         v[0] += a;
         v[1] += b;
@@ -460,8 +467,8 @@ cudaError_t launch_stats(int prec, const void* src, const uint32_t* flags, doubl
 }
 
 cudaError_t launch_check_init(const float* rhoA, const float* rhoB, const float* u, const uint32_t* flags,
-                              double* partials, double* out, const Geom& g, cudaStream_t st) {
-    check_init_kernel<<<kRedBlocks, 256, 0, st>>>(rhoA, rhoB, u, flags, partials, g);
+                              double* partials, double* out, const Geom& g, bool allow_zero, cudaStream_t st) {
+    check_init_kernel<<<kRedBlocks, 256, 0, st>>>(rhoA, rhoB, u, flags, partials, g, allow_zero);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     finish_kernel<<<1, 256, 0, st>>>(partials, kRedBlocks, out);

@@ -230,10 +230,23 @@ __device__ __forceinline__ void cp_async16(uint32_t saddr, const void* gptr) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(gptr) : "memory");
 }
 
-template <typename S, bool MASK>
+// MODEL 0: Shan-Chen (the ring holds the density deviations psi - rho0);
+// MODEL 1: colour gradient (the ring holds the phase field Theta, whose
+// neighbour sums give grad Theta; no mask).
+template <typename S, bool MASK, int MODEL = 0>
 __global__ void __launch_bounds__(kTX * kMaxTY, 1)
 fused_box_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t* __restrict__ flags,
                  float* __restrict__ mom_out, Geom g, Phys p, AsyncPlan P) {
+    constexpr bool CG = MODEL == 1;
+    // what a node contributes to the ring: its density deviations, or Theta
+    auto ring_val = [&](float2 d) -> float2 {
+        if constexpr (CG) {
+            const float t = phase_field(p, d.x, d.y);
+            return make_float2(t, t);
+        } else {
+            return d;
+        }
+    };
     using B = BoxGeo<S>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int RH = P.tymax + 2, RW = kTX + 2;
@@ -382,6 +395,7 @@ fused_box_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t*
         float d[2][packed ? 1 : Q];
         uint32_t w[packed ? Q : 1];
         float j[3];
+        float2 dd;   // density deviations (16-bit colour gradient: the ring holds Theta)
         uint32_t fl;
     };
     Held h0, h1;
@@ -402,13 +416,17 @@ fused_box_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t*
         const int slot = e & 3;
         nxt.fl = kSolid;
         if (own_row) {
-            if constexpr (packed) ring[slot * RH * RW + own_off] = read_node_packed(st_cur, tx, ty, nxt.w, nxt.j, nxt.fl);
-            else ring[slot * RH * RW + own_off] = read_node(st_cur, tx, ty, nxt.d, nxt.fl);
+            if constexpr (packed) {
+                nxt.dd = read_node_packed(st_cur, tx, ty, nxt.w, nxt.j, nxt.fl);
+                ring[slot * RH * RW + own_off] = ring_val(nxt.dd);
+            } else {
+                ring[slot * RH * RW + own_off] = ring_val(read_node(st_cur, tx, ty, nxt.d, nxt.fl));
+            }
         }
         if (has_halo) {
             float dh[2][Q];
             uint32_t fh;
-            ring_at(slot, hly, hlx) = read_node(st_cur, hlx, hly, dh, fh);
+            ring_at(slot, hly, hlx) = ring_val(read_node(st_cur, hlx, hly, dh, fh));
         }
         __syncthreads();   // ring of plane e complete; stage st_cur fully read
         if constexpr (!early) issue(e + ahead, z_iss, st_cur);
@@ -429,8 +447,8 @@ fused_box_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t*
             if constexpr (!packed) {
                 sums(cur.d, dA, dB, j);
             } else {   // own density deviations are already in the ring (same sums)
-                dA = rc[0].x;
-                dB = rc[0].y;
+                dA = CG ? cur.dd.x : rc[0].x;
+                dB = CG ? cur.dd.y : rc[0].y;
 #pragma unroll
                 for (int a = 0; a < 3; ++a) j[a] = cur.j[a];
             }
@@ -448,16 +466,31 @@ fused_box_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t*
                     SA, SB);
             }
             const bool solid = MASK && (cur.fl & kSolid);
-            if (mom_out != nullptr && !solid) store_moments(mom_out, g, own, dA, dB, j, SA, SB);
-            if constexpr (packed)
-                collide_store_g<S, MASK>(
-                    [&](int k, int i) {
-                        if constexpr (sizeof(S) == 2) return Store<S>::part(cur.w[i], k);
-                        else return 0.f;
-                    },
-                    p, dA, dB, j, SA, SB, dst, g, (int)own, solid);
-            else
-                collide_store<S, MASK>(cur.d, p, dA, dB, j, SA, SB, dst, g, (int)own, solid);
+            if constexpr (CG) {
+                // grad Theta = (1 / c_s^2) sum_i w_i c_i Theta(x + c_i)
+                const float gt[3] = {3.0f * SA[0], 3.0f * SA[1], 3.0f * SA[2]};
+                if constexpr (packed)
+                    cg_collide_store_g<S>(
+                        [&](int k, int i) {
+                            if constexpr (sizeof(S) == 2) return Store<S>::part(cur.w[i], k);
+                            else return 0.f;
+                        },
+                        p, dA, dB, j, gt, dst, (int)own);
+                else
+                    cg_collide_store_g<S>([&](int k, int i) { return cur.d[k][i]; }, p, dA, dB, j, gt, dst,
+                                          (int)own);
+            } else {
+                if (mom_out != nullptr && !solid) store_moments(mom_out, g, own, dA, dB, j, SA, SB);
+                if constexpr (packed)
+                    collide_store_g<S, MASK>(
+                        [&](int k, int i) {
+                            if constexpr (sizeof(S) == 2) return Store<S>::part(cur.w[i], k);
+                            else return 0.f;
+                        },
+                        p, dA, dB, j, SA, SB, dst, g, (int)own, solid);
+                else
+                    collide_store<S, MASK>(cur.d, p, dA, dB, j, SA, SB, dst, g, (int)own, solid);
+            }
         }
         if constexpr (packed) {
             ps_lo = ps_mid;
@@ -475,10 +508,10 @@ fused_box_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t*
     cp_wait<0>();
 }
 
-template <typename S, bool MASK>
+template <typename S, bool MASK, int MODEL = 0>
 cudaError_t launch_box_t(const StepLaunch& L, cudaStream_t st) {
     const AsyncPlan& P = L.plan;
-    auto kern = fused_box_kernel<S, MASK>;
+    auto kern = fused_box_kernel<S, MASK, MODEL>;
     static size_t configured = 0;
     if (configured < P.smem) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem);
@@ -511,6 +544,14 @@ cudaError_t launch_t(const StepLaunch& L, cudaStream_t st) {
 
 cudaError_t launch_fused_async(const StepLaunch& L, cudaStream_t st) {
     const bool m = L.flags != nullptr;
+    if (L.p.model == 1) {   // colour gradient: periodic, box kernel only (the caller checks plan.box)
+        switch (L.prec) {
+            case 0: return launch_box_t<float, false, 1>(L, st);
+            case 1: return launch_box_t<__half, false, 1>(L, st);
+            case 2: return launch_box_t<__nv_bfloat16, false, 1>(L, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     if (L.plan.box) {
         switch (L.prec) {
             case 0: return m ? launch_box_t<float, true>(L, st) : launch_box_t<float, false>(L, st);

@@ -163,15 +163,26 @@ collide_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t* _
     float dA, dB, j[3];
     sums(d, dA, dB, j);
     float SA[3], SB[3];
+    const bool cg = p.model == 1;   // colour gradient: the neighbour sums of Theta
     neighbour_sums<kFactoredSums<S>>(
         [&](int dx, int dy, int dz) {
             const int xx = dx > 0 ? wrap_inc(x, g.nx) : (dx < 0 ? wrap_dec(x, g.nx) : x);
             const int yy = dy > 0 ? wrap_inc(y, g.ny) : (dy < 0 ? wrap_dec(y, g.ny) : y);
             const int zz = dz > 0 ? wrap_inc(z, g.nz) : (dz < 0 ? wrap_dec(z, g.nz) : z);
             const long long t = xx + (long long)g.nx * (yy + (long long)g.ny * zz);
-            return make_float2(__ldg(rho + t), __ldg(rho + g.N + t));
+            const float2 r = make_float2(__ldg(rho + t), __ldg(rho + g.N + t));
+            if (cg) {
+                const float th = phase_field(p, r.x, r.y);
+                return make_float2(th, th);
+            }
+            return r;
         },
         SA, SB);
+    if (cg) {
+        const float gt[3] = {3.0f * SA[0], 3.0f * SA[1], 3.0f * SA[2]};
+        cg_collide_store_g<S>([&](int k, int i) { return d[k][i]; }, p, dA, dB, j, gt, dst, (int)s);
+        return;
+    }
     if (mom_out != nullptr) store_moments(mom_out, g, s, dA, dB, j, SA, SB);
     collide_store<S>(d, p, dA, dB, j, SA, SB, dst, g, (int)s);
 }
@@ -197,7 +208,8 @@ cudaError_t launch_step_t(const StepLaunch& L, cudaStream_t st) {
 
 namespace {
 cudaError_t launch_step_kernels(const StepLaunch& L, cudaStream_t st) {
-    if (L.kernel == 0) return launch_fused_async(L, st);
+    // the colour-gradient model runs on the box kernel or the two-pass kernels
+    if (L.kernel == 0 && (L.p.model == 0 || L.plan.box)) return launch_fused_async(L, st);
     const bool m = L.flags != nullptr;
     switch (L.prec) {
         case 0: return m ? launch_step_t<float, true>(L, st) : launch_step_t<float, false>(L, st);

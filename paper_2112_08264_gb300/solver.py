@@ -35,17 +35,22 @@ class Solver:
     "bf16"}, ``kernel`` in {"fused", "two_pass"}, deviation base ``rho0``
     (0 = mean of the initial densities), ``body_force`` g, and checkpoint
     recording for ``backward`` (``ckpt_every`` K, ``ckpt_steps_max``).
+    ``model="colour_gradient"`` selects the paper's colour-gradient model
+    with ``cg=dict(nu=(nu_A, nu_B), sigma=..., beta=...)`` (periodic grids;
+    ``tau`` and ``G`` unused, ``tau`` must still exceed 1/2).
     """
 
     def __init__(self, nx, ny, nz, tau, G, mask=None, prec="fp32", kernel="fused", rho0=(0.0, 0.0),
-                 body_force=(0.0, 0.0, 0.0), ckpt_every=0, ckpt_steps_max=0, device=None, stream=None):
+                 body_force=(0.0, 0.0, 0.0), ckpt_every=0, ckpt_steps_max=0, device=None, stream=None,
+                 model="shan_chen", cg=None):
         L = _lib.lib()
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.shape = (self.nz, self.ny, self.nx)
         self.N = self.nx * self.ny * self.nz
         self.tau, self.G = float(tau), float(G)
         self.prec, self.kernel = prec, kernel
-        self.opt = _lib.options(prec, kernel, rho0, body_force, ckpt_every, ckpt_steps_max)
+        self.model = model
+        self.opt = _lib.options(prec, kernel, rho0, body_force, ckpt_every, ckpt_steps_max, model, cg)
         nbytes = _lib.workspace_bytes(self.nx, self.ny, self.nz, self.opt)
         if nbytes == 0:
             raise ValueError("invalid grid or options")

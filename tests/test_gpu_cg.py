@@ -1,0 +1,138 @@
+"""Colour-gradient model on the GPU against the FP64 oracle
+(``oracle.colour_gradient``), through the C ABI.
+
+Tolerances as for the Shan-Chen path: element-wise states within a few FP32
+ulps of the largest population after one step; densities within 1e-5
+(max-relative) after 50 steps in FP32, 2e-3 with FP16 and 4e-3 with BF16
+storage; the box
+kernel and the two-pass kernels give the same bits; per-component mass and
+total momentum conserved step by step (FP64 totals).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import colour_gradient as cg  # noqa: E402
+from oracle import lb_numpy as ln  # noqa: E402
+from paper_2112_08264_gb300 import Solver, build, inputs  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+CG = dict(nu=(1.0 / 6.0, 1.0 / 10.0), sigma=0.01, beta=0.7)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+
+
+def dev(a):
+    return torch.tensor(np.asarray(a, dtype=np.float32), device="cuda")
+
+
+def fields(shape, seed):
+    """Two phases with diffuse random interfaces and a weak flow (float32-exact)."""
+    nx, ny, nz = shape
+    rng = np.random.default_rng(seed)
+    phi = rng.uniform(-1, 1, (nz, ny, nx))
+    for _ in range(2):   # smooth: interfaces a few nodes wide
+        phi = sum(np.roll(phi, s, axis=a) for a in range(3) for s in (-1, 0, 1)) / 9.0
+    phi = np.clip(3.0 * phi / np.abs(phi).max(), -0.9, 0.9)
+    rA = np.float32(0.5 * (1 + phi)).astype(np.float64)
+    rB = np.float32(0.5 * (1 - phi)).astype(np.float64)
+    u = np.float32(0.01 * rng.uniform(-1, 1, (3, nz, ny, nx))).astype(np.float64)
+    return rA, rB, u
+
+
+def gpu_cg(shape, steps, rA, rB, u=None, **kw):
+    nx, ny, nz = shape
+    s = Solver(nx, ny, nz, 1.0, 0.0, model="colour_gradient", cg=CG, **kw)
+    s.init(dev(rA), dev(rB), dev(u) if u is not None else None)
+    if steps:
+        s.step(steps)
+    return s
+
+
+def oracle_cg(steps, rA, rB, u=None):
+    f = ln.init(rA, rB, u)
+    return cg.run(f, steps, CG["nu"][0], CG["nu"][1], CG["sigma"], CG["beta"])
+
+
+@pytest.mark.parametrize("shape,kernel", [((24, 20, 12), "fused"), ((18, 12, 10), "fused"),
+                                          ((24, 20, 12), "two_pass")])
+def test_single_step_state_elementwise(shape, kernel):
+    rA, rB, u = fields(shape, 7)
+    s = gpu_cg(shape, 1, rA, rB, u, kernel=kernel)
+    got = s.get_state().cpu().numpy().astype(np.float64)
+    s.close()
+    want = ln.to_public(oracle_cg(1, rA, rB, u))
+    err = np.abs(got - want).max() / np.abs(want).max()
+    assert err < 8 * 2.0 ** -24 * 4, err
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_box_and_two_pass_are_bitwise_equal(prec):
+    shape = (32, 16, 12)
+    rA, rB, u = fields(shape, 9)
+    a = gpu_cg(shape, 10, rA, rB, u, kernel="fused", prec=prec)
+    b = gpu_cg(shape, 10, rA, rB, u, kernel="two_pass", prec=prec)
+    assert torch.equal(a.get_state(), b.get_state())
+    a.close()
+    b.close()
+
+
+# BF16 (8 mantissa bits) on colour-gradient deviations, which reach half of
+# w_i rho in segregated phases: 4e-3 (measured 2.1e-3 after 50 steps)
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("fp16", 2e-3), ("bf16", 4e-3)])
+def test_moments_50_steps_and_conservation(prec, tol):
+    shape = (32, 32, 16)
+    rA, rB, u = fields(shape, 3)
+    s = gpu_cg(shape, 0, rA, rB, u, prec=prec)
+    t0 = np.array(s.stats())
+    # FP32: 1e-5 relative; 16-bit storage: the rounding of the stored deviations
+    # (up to a half-ulp of the 16-bit type per population and step) accumulates
+    ctol = 1e-5 if prec == "fp32" else 1e-3
+    for _ in range(5):
+        s.step(10)
+        t = np.array(s.stats())
+        assert abs(t[0] - t0[0]) <= ctol * t0[0] and abs(t[1] - t0[1]) <= ctol * t0[1]
+        assert np.abs(t[2:5] - t0[2:5]).max() <= ctol * t0[0]
+    gA, gB, gu = (x.cpu().numpy().astype(np.float64) for x in s.moments())
+    s.close()
+    oA, oB, ou = cg.moments(oracle_cg(50, rA, rB, u))
+    for a, b in ((gA, oA), (gB, oB)):
+        assert np.abs(a - b).max() / np.abs(b).max() <= tol
+    if prec == "fp32":
+        assert np.abs(gu - ou).max() <= 1e-4 * np.sqrt((ou * ou).sum(axis=0)).max()
+
+
+def test_droplet_against_oracle():
+    """A droplet of pure A in pure B (order parameter +-1, the paper's
+    two-fluid fill) after 300 steps: the same profile as the oracle, mass of
+    A kept, phases segregated (bulk values the oracle reaches: > 0.96 inside
+    r < 5, < 0.01 outside r > 12)."""
+    n = 32
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    r = np.sqrt((x - 15.5) ** 2 + (y - 15.5) ** 2 + (z - 15.5) ** 2)
+    phi = np.where(r < 8, 1.0, -1.0)
+    rA0, rB0 = 0.5 * (1 + phi), 0.5 * (1 - phi)
+    s = gpu_cg((n, n, n), 300, rA0, rB0)
+    gA = s.moments()[0].cpu().numpy().astype(np.float64)
+    s.close()
+    oA = cg.moments(oracle_cg(300, rA0, rB0))[0]
+    assert np.abs(gA - oA).max() < 1e-3
+    assert abs(gA.sum() - rA0.sum()) < 1e-5 * rA0.sum()
+    assert gA[r < 5].min() > 0.95 and gA[r > 12].max() < 0.02
+
+
+def test_rejected_configurations():
+    with pytest.raises(Exception):
+        Solver(16, 16, 16, 1.0, 0.0, model="colour_gradient", cg=CG,
+               mask=inputs.random_mask(16, 16, 16, seed=1, solid_fraction=0.1))
+    with pytest.raises(Exception):
+        Solver(16, 16, 16, 1.0, 0.0, model="colour_gradient", cg=CG, kernel="fused_reg")
+    with pytest.raises(Exception):
+        Solver(16, 16, 16, 1.0, 0.0, model="colour_gradient", cg=CG, ckpt_every=4, ckpt_steps_max=8)
