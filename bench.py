@@ -168,6 +168,16 @@ def workload(name, grid=None):
         rA, rB = inputs.random_order_parameter(n, n, n, seed=1234)
         return dict(shape=(n, n, n), tau=1.0, G=0.65, rA=rA, rB=rB, mask=None,
                     desc="%d^3 periodic, random order parameter +-0.9 per site (seed 1234), tau=1, G=0.65" % n)
+    if name == "cg256":
+        n = grid or 256
+        rA, rB = inputs.random_order_parameter(n, n, n, seed=1234, phi0=1.0)
+        cg = dict(nu=(1.0 / 6.0, 1.0 / 6.0), sigma=0.01, beta=0.7)
+        return dict(shape=(n, n, n), tau=1.0, G=0.0, rA=rA, rB=rB, mask=None, model="colour_gradient", cg=cg,
+                    solver_kw=dict(model="colour_gradient", cg=cg),
+                    metric="GLUPS, 2-comp D3Q19 colour-gradient %d^3 (the paper's two-fluid case); "
+                           "%% of HBM roofline" % n,
+                    desc="colour gradient %d^3 periodic, random order parameter +-1 per site (seed 1234), "
+                         "nu_A = nu_B = 1/6, sigma = 0.01, beta = 0.7" % n)
     if name == "spinodal512":
         n = 512
         rA, rB = inputs.spinodal(n, n, n, seed=1234)
@@ -182,7 +192,7 @@ def time_device(W, prec, kernel, steps, warmup, events_per_step=False):
     import torch
     from paper_2112_08264_gb300 import Solver
     nx, ny, nz = W["shape"]
-    s = Solver(nx, ny, nz, W["tau"], W["G"], mask=W["mask"], prec=prec, kernel=kernel)
+    s = Solver(nx, ny, nz, W["tau"], W["G"], mask=W["mask"], prec=prec, kernel=kernel, **W.get("solver_kw", {}))
     dA = torch.tensor(W["rA"], dtype=torch.float32, device="cuda")
     dB = torch.tensor(W["rB"], dtype=torch.float32, device="cuda")
     s.init(dA, dB)
@@ -210,7 +220,7 @@ def time_e2e(W, prec, kernel, steps):
     import torch
     from paper_2112_08264_gb300 import Solver, run_host
     nx, ny, nz = W["shape"]
-    s = Solver(nx, ny, nz, W["tau"], W["G"], mask=W["mask"], prec=prec, kernel=kernel)
+    s = Solver(nx, ny, nz, W["tau"], W["G"], mask=W["mask"], prec=prec, kernel=kernel, **W.get("solver_kw", {}))
     rA = W["rA"].astype(np.float32)
     rB = W["rB"].astype(np.float32)
     run_host(rA, rB, 3, W["tau"], W["G"], solver=s)      # warm
@@ -279,9 +289,41 @@ def oracle_sample(shape, tau, G, budget_s, min_steps=1, max_steps=1000, per_step
     return rA, rB, nzs, steps, cores
 
 
+def cg_oracle_sample(W, budget_s=None, per_step_budget=None):
+    """Colour-gradient oracle (numpy, one thread) on a periodic slab of the
+    workload's recipe, sized like oracle_sample."""
+    from oracle import colour_gradient as cgo
+    from oracle import lb_numpy as ln
+    from paper_2112_08264_gb300 import inputs
+    nx, ny, nz = W["shape"]
+    c = W["cg"]
+    rA, rB = inputs.random_order_parameter(nx, ny, 2, seed=1234, phi0=1.0)
+    f = ln.init(rA, rB)
+    t0 = time.perf_counter()
+    cgo.step(f, c["nu"][0], c["nu"][1], c["sigma"], c["beta"])
+    rate = nx * ny * 2 / max(time.perf_counter() - t0, 1e-6)
+    if per_step_budget is not None:
+        nzs, steps = int(max(1, min(nz, per_step_budget * rate / (nx * ny)))), None
+    else:
+        nzs = int(max(2, min(nz, 16)))
+        steps = int(max(1, min(1000, budget_s * rate / (nx * ny * nzs))))
+    rA, rB = inputs.random_order_parameter(nx, ny, nzs, seed=1234, phi0=1.0)
+    step = lambda g: cgo.step(g, c["nu"][0], c["nu"][1], c["sigma"], c["beta"])
+    return ln.init(rA, rB), step, nzs, steps
+
+
 def run_cpu_baseline(W, budget_s=15.0):
     import oracle
     nx, ny, nz = W["shape"]
+    if W.get("model") == "colour_gradient":
+        f, step, nzs, steps = cg_oracle_sample(W, budget_s)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            f = step(f)
+        dt = time.perf_counter() - t0
+        return {"value": nx * ny * nzs * steps / dt / 1e9, "unit": "GLUPS", "cores": 1, "kind": "oracle",
+                "sample": "%d FP64 colour-gradient oracle steps (numpy, one thread) on a %dx%dx%d periodic slab "
+                          "of the workload (%.1f s)" % (steps, nx, ny, nzs, dt)}
     rA, rB, nzs, steps, cores = oracle_sample(W["shape"], W["tau"], W["G"], budget_s)
     f = oracle.init(rA, rB)
     t0 = time.perf_counter()
@@ -311,17 +353,22 @@ def main_reference(args, world, rank):
     import oracle
     # each step a bounded slab sample sized so warmup + steps take ~150 s
     per_step = 150.0 / max(1, args.steps + args.warmup)
-    rA, rB, nzs, _, cores = oracle_sample(W["shape"], W["tau"], W["G"], None, per_step_budget=per_step)
-    f = oracle.init(rA, rB)
+    if W.get("model") == "colour_gradient":
+        f, step, nzs, _ = cg_oracle_sample(W, per_step_budget=per_step)
+        cores = 1
+    else:
+        rA, rB, nzs, _, cores = oracle_sample(W["shape"], W["tau"], W["G"], None, per_step_budget=per_step)
+        f = oracle.init(rA, rB)
+        step = lambda g: oracle.step(g, W["tau"], W["G"])
     for _ in range(args.warmup):
-        f = oracle.step(f, W["tau"], W["G"])
+        f = step(f)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        f = oracle.step(f, W["tau"], W["G"])
+        f = step(f)
     dt = time.perf_counter() - t0
     glups = nx * ny * nzs * args.steps / dt / 1e9
     sample = "each step: one FP64 oracle step on a %dx%dx%d periodic slab of the workload" % (nx, ny, nzs)
-    line = {"impl": "reference", "metric": METRIC, "value": glups, "unit": "GLUPS", "n_gpus": args.gpus,
+    line = {"impl": "reference", "metric": W.get("metric", METRIC), "value": glups, "unit": "GLUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": W["desc"], "sample": sample},
@@ -338,7 +385,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="spinodal256",
-                    choices=["spinodal256", "colloid256", "orderparam256", "spinodal512"])
+                    choices=["spinodal256", "colloid256", "orderparam256", "cg256", "spinodal512"])
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--kernel", default="fused", choices=["fused", "two_pass"])
     ap.add_argument("--grid", type=int, default=None, help="override the spinodal grid size (profiling)")
@@ -386,10 +433,13 @@ def main():
         alg_bytes * N / (ms / 1e3 / args.steps) / 1e9
     tps = traffic_per_site(args.prec) if (args.kernel == "fused" and W["mask"] is None) else None
 
+    # the paper prints a 256^3 number only for its colour-gradient runs: 0.601
+    # GLUPS, one V100, plain two-pass step (Table cg); context, other hardware
+    vs_base = glups / 0.601 if (W.get("model") == "colour_gradient" and (nx, ny, nz) == (256, 256, 256)) else None
     line = {
-        "metric": METRIC, "value": glups, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
+        "metric": W.get("metric", METRIC), "value": glups, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": DTYPE_TAG[args.prec], "data": "synthetic",
+        "vs_baseline": vs_base, "dtype": DTYPE_TAG[args.prec], "data": "synthetic",
         "config": {"workload": W["desc"], "grid": [nx, ny, nz], "prec": args.prec, "kernel": args.kernel,
                    "parallelism": "replicas" if world > 1 else "single-gpu",
                    "l2": "state %.2f GB per buffer > 129 MB L2; no flush needed" % (38 * N * (bps / 76) / 1e9),
@@ -416,6 +466,8 @@ def main():
         for prec, kern in (("fp16", "fused"), ("bf16", "fused"), ("fp32", "two_pass"), ("fp32", "fused_reg")):
             if (prec, kern) == (args.prec, args.kernel):
                 continue
+            if kern == "fused_reg" and W.get("model") == "colour_gradient":
+                continue   # the register kernel implements Shan-Chen only
             vms, vinfo, _ = time_device(W, prec, kern, args.steps, args.warmup)
             vstep = vms / 1e3 / args.steps
             vb = BYTES_PER_SITE[prec] * (fluid if W["mask"] is not None else 1.0)
