@@ -245,22 +245,34 @@ __device__ __forceinline__ void cg_collide_store_g(DGet&& dget, const Phys& p, f
     const float e = (rA * p.rho0[1] - p.rho0[0] * rB) * inv;
     const float fa = rA * inv, fb = rB * inv;
     S* out = dst + blk_base((uint32_t)own);
-    static_for<0, Q>([&](auto I) {
-        constexpr int i = decltype(I)::value;
+    {   // rest velocity: c = 0, so no recolouring
+        constexpr float w = 1.0f / 3.0f;
+        const float pert = hA * ((2.0f / 9.0f) * gn);
+        const float D = (om1 * dget(0, 0) + omega * w * (dA - rA * uu15) + pert) +
+                        (om1 * dget(1, 0) + omega * w * (dB - rB * uu15) + pert);
+        Store<S>::st2(out, w * e + fa * D, -w * e + fb * D);
+    }
+    // opposite pairs (i, i + 1): c.u, c.grad Theta change sign, the
+    // perturbation is the same and the recolouring term flips
+    static_for<0, 9>([&](auto M) {
+        constexpr int i = 2 * decltype(M)::value + 1;
         float cu = 0.f, cg = 0.f;
         if constexpr (Vel<i>::x != 0) { cu += Vel<i>::x * u[0]; cg += Vel<i>::x * gt[0]; }
         if constexpr (Vel<i>::y != 0) { cu += Vel<i>::y * u[1]; cg += Vel<i>::y * gt[1]; }
         if constexpr (Vel<i>::z != 0) { cu += Vel<i>::z * u[2]; cg += Vel<i>::z * gt[2]; }
         constexpr float w = wgt<i>();
-        constexpr float Bi = Vel<i>::c2 == 0 ? -2.0f / 9.0f : (Vel<i>::c2 == 1 ? 1.0f / 54.0f : 1.0f / 27.0f);
-        constexpr float wrc = Vel<i>::c2 == 2 ? w * 0.70710678f : w;   // w_i / |c_i| (cg = 0 at rest)
-        const float poly = cu * (3.0f + 4.5f * cu) - uu15;
+        constexpr float Bi = Vel<i>::c2 == 1 ? 1.0f / 54.0f : 1.0f / 27.0f;
+        constexpr float wrc = Vel<i>::c2 == 2 ? w * 0.70710678f : w;   // w_i / |c_i|
+        const float even = 4.5f * cu * cu - uu15, odd = 3.0f * cu;
         const float pert = hA * (w * cg * cg * q - Bi * gn);
-        const float d2A = om1 * dget(0, i) + omega * w * (dA + rA * poly) + pert;
-        const float d2B = om1 * dget(1, i) + omega * w * (dB + rB * poly) + pert;
-        const float D = d2A + d2B;
-        const float X = kc * wrc * cg;
-        Store<S>::st2(out + i * (2 * kBlk), w * e + fa * D + X, -w * e + fb * D - X);
+        const float ow = omega * w;
+        const float bA = ow * (dA + rA * even) + pert, oA = ow * rA * odd;
+        const float bB = ow * (dB + rB * even) + pert, oB = ow * rB * odd;
+        const float Di = (om1 * dget(0, i) + bA + oA) + (om1 * dget(1, i) + bB + oB);
+        const float Dj = (om1 * dget(0, i + 1) + bA - oA) + (om1 * dget(1, i + 1) + bB - oB);
+        const float X = kc * wrc * cg, we = w * e;
+        Store<S>::st2(out + i * (2 * kBlk), we + fa * Di + X, -we + fb * Di - X);
+        Store<S>::st2(out + (i + 1) * (2 * kBlk), we + fa * Dj - X, -we + fb * Dj + X);
     });
 }
 
