@@ -87,6 +87,22 @@ def lib():
     for name in ("lb_create", "lb_set_stream", "lb_init", "lb_step", "lb_moments", "lb_stats",
                  "lb_get_state", "lb_set_state", "lb_backward", "lb_launch_info"):
         getattr(L, name).restype = ctypes.c_int
+    # one-component BGK (include/lb1.h)
+    L.lb1_workspace_bytes.argtypes = [ctypes.c_int] * 4
+    L.lb1_workspace_bytes.restype = ctypes.c_size_t
+    L.lb1_create.argtypes = ([ctypes.c_int] * 3 + [ctypes.c_float, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                                   _VP, ctypes.c_size_t, _VP, ctypes.POINTER(_VP)])
+    L.lb1_init.argtypes = [_VP, _FP, _FP]
+    L.lb1_step.argtypes = [_VP, ctypes.c_int]
+    L.lb1_moments.argtypes = [_VP, _FP, _FP]
+    L.lb1_stats.argtypes = [_VP, ctypes.POINTER(ctypes.c_double)]
+    L.lb1_get_state.argtypes = [_VP, _FP]
+    L.lb1_launch_info.argtypes = [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    L.lb1_destroy.argtypes = [_VP]
+    L.lb1_destroy.restype = None
+    for name in ("lb1_create", "lb1_init", "lb1_step", "lb1_moments", "lb1_stats", "lb1_get_state",
+                 "lb1_launch_info"):
+        getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
 

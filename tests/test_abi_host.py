@@ -1,5 +1,5 @@
 """Host-side checks of the C ABI that need no GPU: the library builds and
-loads, exports every function ``include/lb.h`` declares, sizes workspaces and
+loads, exports every function ``include/*.h`` declares, sizes workspaces and
 rejects invalid arguments before touching a device."""
 import ctypes
 import os
@@ -9,7 +9,8 @@ import pytest
 
 from paper_2112_08264_gb300 import _lib, build
 
-HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "lb.h")
+INCLUDE = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include")
+HEADERS = sorted(os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h"))
 
 
 @pytest.fixture(scope="module")
@@ -19,17 +20,33 @@ def L():
 
 
 def declared_functions():
-    src = open(HEADER).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"\b(lb_[a-z_0-9]+)\s*\(", src)
-    return sorted(set(names))
+    names = set()
+    for h in HEADERS:
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names.update(re.findall(r"\b(lb1?_[a-z_0-9]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_header_declares_the_boundary():
     names = declared_functions()
     for must in ("lb_create", "lb_init", "lb_step", "lb_moments", "lb_backward", "lb_stats",
-                 "lb_get_state", "lb_set_state", "lb_destroy", "lb_workspace_bytes", "lb_status_str"):
+                 "lb_get_state", "lb_set_state", "lb_destroy", "lb_workspace_bytes", "lb_status_str",
+                 "lb1_create", "lb1_init", "lb1_step", "lb1_moments", "lb1_stats", "lb1_get_state"):
         assert must in names
+
+
+def test_single_fluid_workspace_and_rejections(L):
+    L.lb1_workspace_bytes.restype = ctypes.c_size_t
+    n = 32 ** 3
+    wb = L.lb1_workspace_bytes(32, 32, 32, 0)
+    assert wb >= 2 * 19 * n * 4
+    assert 0 < L.lb1_workspace_bytes(32, 32, 32, 1) < wb
+    assert L.lb1_workspace_bytes(2, 32, 32, 0) == 0
+    assert L.lb1_workspace_bytes(8, 8, 8, 7) == 0
+    h = ctypes.c_void_p()
+    # tau <= 1/2 and a missing workspace are rejected before any device call
+    assert L.lb1_create(16, 16, 16, ctypes.c_float(0.5), None, 0, None, 0, None, ctypes.byref(h)) == 1
+    assert L.lb1_create(16, 16, 16, ctypes.c_float(1.0), None, 0, None, 0, None, ctypes.byref(h)) == 1
 
 
 def test_library_exports_every_declared_symbol(L):
