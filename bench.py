@@ -178,6 +178,13 @@ def workload(name, grid=None):
                            "%% of HBM roofline" % n,
                     desc="colour gradient %d^3 periodic, random order parameter +-1 per site (seed 1234), "
                          "nu_A = nu_B = 1/6, sigma = 0.01, beta = 0.7" % n)
+    if name == "single256":
+        n = grid or 256
+        rng = np.random.default_rng(1234)
+        rho = 1.0 + 0.05 * rng.uniform(-1, 1, (n, n, n))
+        return dict(shape=(n, n, n), tau=1.0, G=0.0, rA=rho, rB=None, mask=None, model="single",
+                    metric="GLUPS, 1-comp D3Q19 BGK %d^3 (the paper's single-fluid case); %% of HBM roofline" % n,
+                    desc="single fluid %d^3 periodic, tau=1, rho=1+0.05U(-1,1) seed 1234, u=0" % n)
     if name == "spinodal512":
         n = 512
         rA, rB = inputs.spinodal(n, n, n, seed=1234)
@@ -356,6 +363,9 @@ def main_reference(args, world, rank):
     if W.get("model") == "colour_gradient":
         f, step, nzs, _ = cg_oracle_sample(W, per_step_budget=per_step)
         cores = 1
+    elif W.get("model") == "single":
+        f, step, nzs, _ = single_oracle_sample(W, per_step_budget=per_step)
+        cores = 1
     else:
         rA, rB, nzs, _, cores = oracle_sample(W["shape"], W["tau"], W["G"], None, per_step_budget=per_step)
         f = oracle.init(rA, rB)
@@ -378,6 +388,136 @@ def main_reference(args, world, rank):
     return 0
 
 
+def time_single(W, prec, steps, warmup):
+    """Device-resident timing of the one-component step (CUDA events on its stream)."""
+    import torch
+    from paper_2112_08264_gb300 import SingleFluid
+    nx, ny, nz = W["shape"]
+    s = SingleFluid(nx, ny, nz, W["tau"], prec=prec)
+    s.init(torch.tensor(W["rA"], dtype=torch.float32, device="cuda"))
+    s.step(warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(s.stream):
+        e0.record(s.stream)
+        s.step(steps)
+        e1.record(s.stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    info, st = s.launch_info(), s.stats()
+    s.close()
+    torch.cuda.synchronize()
+    return ms, info, st
+
+
+def e2e_single(W, prec, steps):
+    """Host rho -> pinned H2D -> lb1_init -> steps -> moments -> D2H, timed on the host."""
+    import torch
+    from paper_2112_08264_gb300 import SingleFluid
+    nx, ny, nz = W["shape"]
+    s = SingleFluid(nx, ny, nz, W["tau"], prec=prec)
+    host = torch.from_numpy(W["rA"].astype(np.float32)).pin_memory()
+    out_r = torch.empty(host.shape, dtype=torch.float32).pin_memory()
+    out_u = torch.empty((3,) + tuple(host.shape), dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    d = host.to("cuda", non_blocking=True)
+    s.init(d)
+    s.step(steps)
+    r, u = s.moments()
+    out_r.copy_(r, non_blocking=True)
+    out_u.copy_(u, non_blocking=True)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    s.close()
+    return dt, host.numel() * 4, (out_r.numel() + out_u.numel()) * 4
+
+
+def single_oracle_sample(W, budget_s=None, per_step_budget=None):
+    from oracle import single_bgk as sb
+    nx, ny, nz = W["shape"]
+    rng = np.random.default_rng(1234)
+    probe = sb.WEIGHTS[:, None, None, None] * (1.0 + 0.05 * rng.uniform(-1, 1, (2, ny, nx)))
+    t0 = time.perf_counter()
+    sb.step(probe, W["tau"])
+    rate = nx * ny * 2 / max(time.perf_counter() - t0, 1e-6)
+    if per_step_budget is not None:
+        nzs, steps = int(max(1, min(nz, per_step_budget * rate / (nx * ny)))), None
+    else:
+        nzs = int(max(2, min(nz, 16)))
+        steps = int(max(1, min(1000, budget_s * rate / (nx * ny * nzs))))
+    f = sb.WEIGHTS[:, None, None, None] * W["rA"][:nzs]
+    return f, (lambda g: sb.step(g, W["tau"])), nzs, steps
+
+
+def main_single(args, W, world, rank, local):
+    """The one-component step: same JSON contract as the two-component line."""
+    nx, ny, nz = W["shape"]
+    N = nx * ny * nz
+    peak, peak_kind = measured_peaks()
+    barrier(world)
+    with ClockSampler(local) as clk:
+        ms, info, st = time_single(W, args.prec, args.steps, args.warmup)
+    clocks = clk.summary()
+    if not clocks_ok(clocks):
+        with ClockSampler(local) as clk:
+            ms, info, st = time_single(W, args.prec, args.steps, args.warmup)
+        clocks = clk.summary()
+        clocks["remeasured"] = True
+    barrier(world)
+    glups, step_s = replica_throughput(ms, args.steps, N, world)
+    bps = BYTES_PER_SITE[args.prec] // 2   # 19 populations read and written once
+    achieved = bps * N / (ms / 1e3 / args.steps) / 1e9
+    line = {
+        "metric": W["metric"], "value": glups, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
+        # the paper's single-V100 fused figure at 256^3 (Table 1); context, other hardware
+        "vs_baseline": glups / 2.011 if (nx, ny, nz) == (256, 256, 256) else None,
+        "dtype": DTYPE_TAG[args.prec], "data": "synthetic",
+        "config": {"workload": W["desc"], "grid": [nx, ny, nz], "prec": args.prec, "kernel": "fused",
+                   "parallelism": "replicas" if world > 1 else "single-gpu",
+                   "l2": "state %.2f GB per buffer > 129 MB L2; no flush needed" % (19 * N * (bps / 38) / 1e9),
+                   "launch": info},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": peak_kind, "algorithmic_bytes_per_site": bps,
+                     "timed": "the step kernel (one launch per step)", "traffic": None},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+        "conserved_totals": [float(x) for x in st],
+    }
+    if rank == 0 and not args.no_e2e:
+        dt, h2d, d2h = e2e_single(W, args.prec, args.steps)
+        line["e2e"] = {"value": N * args.steps / dt / 1e9, "unit": "GLUPS", "h2d_bytes_per_step": h2d / args.steps,
+                       "d2h_bytes_per_step": d2h / args.steps,
+                       "what": "host rho -> pinned H2D -> lb1_init -> %d steps -> moments -> D2H" % args.steps}
+    if rank == 0 and not args.no_variants:
+        var = {}
+        for prec in ("fp32", "fp16", "bf16"):
+            if prec == args.prec:
+                continue
+            vms, _, _ = time_single(W, prec, args.steps, args.warmup)
+            vstep = vms / 1e3 / args.steps
+            var[prec] = {"GLUPS": N / vstep / 1e9, "ms_per_step": vstep * 1e3,
+                         "hbm_frac_of_%s" % peak_kind: BYTES_PER_SITE[prec] // 2 * N / vstep / 1e9 / peak}
+        line["variants"] = var
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        f, step, nzs, steps = single_oracle_sample(W, 15.0)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            f = step(f)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": nx * ny * nzs * steps / dt / 1e9, "unit": "GLUPS", "cores": 1,
+                                "kind": "oracle",
+                                "sample": "%d FP64 one-component oracle steps (numpy, one thread) on a %dx%dx%d "
+                                          "periodic slab of the workload (%.1f s)" % (steps, nx, ny, nzs, dt)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -385,7 +525,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="spinodal256",
-                    choices=["spinodal256", "colloid256", "orderparam256", "cg256", "spinodal512"])
+                    choices=["spinodal256", "colloid256", "orderparam256", "cg256", "single256", "spinodal512"])
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--kernel", default="fused", choices=["fused", "two_pass"])
     ap.add_argument("--grid", type=int, default=None, help="override the spinodal grid size (profiling)")
@@ -405,6 +545,8 @@ def main():
     if rank == 0 or world > 1:
         build.build()
     W = workload(args.config, args.grid)
+    if W.get("model") == "single":
+        return main_single(args, W, world, rank, local)
     nx, ny, nz = W["shape"]
     N = nx * ny * nz
     peak, peak_kind = measured_peaks()
