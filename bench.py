@@ -480,7 +480,8 @@ def main_single(args, W, world, rank, local):
                    "launch": info},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": peak_kind, "algorithmic_bytes_per_site": bps,
-                     "timed": "the step kernel (one launch per step)", "traffic": None},
+                     "timed": "the step kernel (one launch per step)",
+                     "traffic": (traffic_per_site("single_" + args.prec) or 0) * N or None},
         "gpu_launches": args.steps,
         "clocks": clocks,
         "conserved_totals": [float(x) for x in st],
