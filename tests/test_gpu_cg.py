@@ -136,3 +136,24 @@ def test_rejected_configurations():
         Solver(16, 16, 16, 1.0, 0.0, model="colour_gradient", cg=CG, kernel="fused_reg")
     with pytest.raises(Exception):
         Solver(16, 16, 16, 1.0, 0.0, model="colour_gradient", cg=CG, ckpt_every=4, ckpt_steps_max=8)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_full_size_256_tiled_state(prec):
+    """256^3 in the benchmark's launch configuration (the box kernel, one
+    launch per step): a random 16^3 periodic state tiled 16 times per axis
+    evolves exactly as the oracle's 16^3 run, at every one of the 16.8M sites."""
+    n, p, steps = 256, 16, 3
+    rA, rB, u = fields((p, p, p), 21)
+    reps = (n // p,) * 3
+    s = Solver(n, n, n, 1.0, 0.0, model="colour_gradient", cg=CG, prec=prec)
+    assert s.launch_info()["launches_per_step"] == 1
+    big = lambda a: torch.tensor(np.asarray(a, np.float32), device="cuda").repeat(*reps).contiguous()
+    s.init(big(rA), big(rB), torch.stack([big(u[a]) for a in range(3)]).contiguous())
+    s.step(steps)
+    got = s.get_state()
+    want = ln.to_public(oracle_cg(steps, rA, rB, u))
+    want_t = torch.tensor(want.astype(np.float32), device="cuda").repeat(1, 1, *reps)
+    tol = {"fp32": 4e-7, "fp16": 5e-4}[prec] * float(want_t.abs().max())
+    assert float((got - want_t).abs().max()) <= tol
+    s.close()
