@@ -155,24 +155,25 @@ def workload(name, grid=None):
     if name == "spinodal256":
         n = grid or 256
         rA, rB = inputs.spinodal(n, n, n, seed=1234)
-        return dict(shape=(n, n, n), tau=1.0, G=0.65, rA=rA, rB=rB, mask=None,
+        return dict(shape=(n, n, n), tau=1.0, G=0.65, rA=rA, rB=rB, mask=None, traffic="" if n == 256 else None,
                     desc="spinodal %d^3 periodic, tau=1, G=0.65, rho_A=0.5+0.05U(-1,1) seed 1234" % n)
     if name == "colloid256":
         n = 256
         rA, rB = inputs.spinodal(n, n, n, seed=1234)
         mask, _ = inputs.colloid_mask(n, n, n, n_spheres=4000, radius=5.0, seed=4321)
-        return dict(shape=(n, n, n), tau=1.0, G=0.65, rA=rA, rB=rB, mask=mask,
+        return dict(shape=(n, n, n), tau=1.0, G=0.65, rA=rA, rB=rB, mask=mask, traffic="colloid_",
                     desc="256^3, 4000 static spheres R=5 (seed 4321), halfway bounce-back")
     if name == "orderparam256":
         n = grid or 256
         rA, rB = inputs.random_order_parameter(n, n, n, seed=1234)
-        return dict(shape=(n, n, n), tau=1.0, G=0.65, rA=rA, rB=rB, mask=None,
+        return dict(shape=(n, n, n), tau=1.0, G=0.65, rA=rA, rB=rB, mask=None, traffic="" if n == 256 else None,
                     desc="%d^3 periodic, random order parameter +-0.9 per site (seed 1234), tau=1, G=0.65" % n)
     if name == "cg256":
         n = grid or 256
         rA, rB = inputs.random_order_parameter(n, n, n, seed=1234, phi0=1.0)
         cg = dict(nu=(1.0 / 6.0, 1.0 / 6.0), sigma=0.01, beta=0.7)
         return dict(shape=(n, n, n), tau=1.0, G=0.0, rA=rA, rB=rB, mask=None, model="colour_gradient", cg=cg,
+                    traffic="cg_" if n == 256 else None,
                     solver_kw=dict(model="colour_gradient", cg=cg),
                     metric="GLUPS, 2-comp D3Q19 colour-gradient %d^3 (the paper's two-fluid case); "
                            "%% of HBM roofline" % n,
@@ -574,7 +575,9 @@ def main():
     kernel_s = (ms / 1e3) / (args.steps * info["launches_per_step"])
     achieved = alg_bytes * N / kernel_s / 1e9 if info["launches_per_step"] == 1 else \
         alg_bytes * N / (ms / 1e3 / args.steps) / 1e9
-    tps = traffic_per_site(args.prec) if (args.kernel == "fused" and W["mask"] is None) else None
+    # measured DRAM bytes per site of this workload's step (ncu, 256^3), when committed
+    tkey = W.get("traffic")
+    tps = traffic_per_site(tkey + args.prec) if (args.kernel == "fused" and tkey is not None) else None
 
     # the paper prints a 256^3 number only for its colour-gradient runs: 0.601
     # GLUPS, one V100, plain two-pass step (Table cg); context, other hardware

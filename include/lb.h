@@ -105,8 +105,9 @@ void lb_default_options(lb_options* opt);
 
 /* Bytes of device workspace lb_create needs for this grid and options
  * (two population buffers, density scratch, reduction scratch, the solid
- * flags and the bounce-back link list (up to N links) when a mask is used --
- * counted always -- and, when opt->ckpt_every > 0, checkpoints plus the
+ * flags and the bounce-back link lists (up to N links of each kind: crossing
+ * a tile of the step kernel, and inside one) when a mask is used -- counted
+ * always -- and, when opt->ckpt_every > 0, checkpoints plus the
  * adjoint's buffers). opt may be NULL (defaults). Returns 0 for invalid
  * sizes. Pure host function. */
 size_t lb_workspace_bytes(int nx, int ny, int nz, const lb_options* opt);
@@ -181,6 +182,15 @@ lb_status lb_backward(lb_ctx* ctx, const float* d_dL_drhoA, const float* d_dL_dr
  * launches per lb_step(1), and the tile/grid shape chosen at lb_create. */
 lb_status lb_launch_info(const lb_ctx* ctx, int* launches_per_step, int* grid_blocks,
                          int* block_threads, int* z_split);
+
+/* Bounce-back links of the mask (pairs of a fluid node x and a direction i
+ * with x + c_i solid, Eq. LADDFLBE), as lb_create arranged them: *listed =
+ * links in the per-velocity list of the bounce-back pass (-1: too many, the
+ * pass scans every site; 0 without a mask); *in_tile = links grouped by tile
+ * of the fused step kernel (target in the same tile and z-chunk as the
+ * source); *in_kernel = 1 when lb_step copies those inside the step kernel,
+ * 0 when it runs them as a pass of their own. Any pointer may be NULL. */
+lb_status lb_link_info(const lb_ctx* ctx, long long* listed, long long* in_tile, int* in_kernel);
 
 /* Allocation-free moments of a caller's population field. The paper has no
  * counterpart; this entry point exists for callers that may not allocate

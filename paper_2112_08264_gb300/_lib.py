@@ -75,6 +75,8 @@ def lib():
     L.lb_steps_done.restype = ctypes.c_longlong
     L.lb_backward.argtypes = [_VP, _FP, _FP, _FP, _FP, ctypes.POINTER(ctypes.c_double)]
     L.lb_launch_info.argtypes = [_VP] + [ctypes.POINTER(ctypes.c_int)] * 4
+    L.lb_link_info.argtypes = [_VP, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                               ctypes.POINTER(ctypes.c_int)]
     L.lb_moments_noalloc.argtypes = ([ctypes.c_int] * 3 + [ctypes.c_float, ctypes.POINTER(ctypes.c_double),
                                                              _FP, _VP, _FP, _FP, _FP, _VP])
     L.lb_moments_noalloc.restype = ctypes.c_int
@@ -85,7 +87,7 @@ def lib():
     L.lb_last_error.argtypes = []
     L.lb_last_error.restype = ctypes.c_char_p
     for name in ("lb_create", "lb_set_stream", "lb_init", "lb_step", "lb_moments", "lb_stats",
-                 "lb_get_state", "lb_set_state", "lb_backward", "lb_launch_info"):
+                 "lb_get_state", "lb_set_state", "lb_backward", "lb_launch_info", "lb_link_info"):
         getattr(L, name).restype = ctypes.c_int
     # one-component BGK (include/lb1.h)
     L.lb1_workspace_bytes.argtypes = [ctypes.c_int] * 4

@@ -76,6 +76,70 @@ __device__ __forceinline__ long long nb_index(const Geom& g, int x, int y, int z
     return xx + (long long)g.nx * (yy + (long long)g.ny * zz);
 }
 
+// Tiling of the box step kernel: strips of kTileX columns (ncols of them),
+// R bands of rows (band c covers rows [c ny / R, (c + 1) ny / R)), and
+// z-chunks of zchunk planes. R == 0: no tiling.
+constexpr int kTileX = 32;
+struct TileMap {
+    int ncols = 0, R = 0, zchunk = 0;
+};
+// band of row y: the largest c with c ny / R <= y (integer division)
+__host__ __device__ __forceinline__ int band_of(int y, int ny, int R) {
+    return (int)(((long long)(y + 1) * R - 1) / ny);
+}
+__host__ __device__ __forceinline__ int band_start(int c, int ny, int R) {
+    return (int)(((long long)c * ny) / R);
+}
+
+// Bounce-back links grouped by (tile, source plane): list (b, z) is
+// ent[start[b nz + z], start[b nz + z + 1]). An entry packs the source node's
+// place in its tile and the velocity: lx | ly << 5 | i << 9 (lx < 32,
+// ly < 16, 1 <= i < Q).
+struct LinkTiles {
+    const uint32_t* start = nullptr;
+    const uint16_t* ent = nullptr;
+};
+__host__ __device__ __forceinline__ uint16_t link_entry(int lx, int ly, int i) {
+    return (uint16_t)(lx | (ly << 5) | (i << 9));
+}
+
+// c_i by component for a velocity known only at run time: two bits per
+// velocity holding c + 1, packed from the Vel table.
+template <int AX, int I = 0>
+__host__ __device__ constexpr unsigned long long packed_axis() {
+    if constexpr (I == Q) {
+        return 0ull;
+    } else {
+        constexpr int c = AX == 0 ? Vel<I>::x : (AX == 1 ? Vel<I>::y : Vel<I>::z);
+        return ((unsigned long long)(c + 1) << (2 * I)) | packed_axis<AX, I + 1>();
+    }
+}
+template <int AX>
+__host__ __device__ __forceinline__ int vel_c(int i) {
+    return (int)((packed_axis<AX>() >> (2 * i)) & 3ull) - 1;
+}
+// opposite of a moving velocity (the public order pairs 1-2, 3-4, ..., 17-18)
+__host__ __device__ __forceinline__ int vel_opp(int i) { return ((i - 1) ^ 1) + 1; }
+
+// Element offsets (component A of the pair) of a tile link's two slots:
+// velocity i at the source node (x0 + lx, y0 + ly, z) and velocity opp(i) at
+// the solid node x + c_i (periodic in x and y; the builder keeps only links
+// whose target plane lies inside the source's z-chunk).
+struct LinkSlots {
+    size_t src, dst;
+};
+__device__ __forceinline__ LinkSlots tile_link_slots(uint32_t e, int x0, int y0, int z, const Geom& g) {
+    const int i = (int)(e >> 9);
+    const int x = x0 + (int)(e & 31u), y = y0 + (int)((e >> 5) & 15u);
+    int tx = x + vel_c<0>(i), ty = y + vel_c<1>(i);
+    tx = tx < 0 ? tx + g.nx : (tx >= g.nx ? tx - g.nx : tx);
+    ty = ty < 0 ? ty + g.ny : (ty >= g.ny ? ty - g.ny : ty);
+    const int tz = z + vel_c<2>(i);
+    const uint32_t s = (uint32_t)x + (uint32_t)g.nx * ((uint32_t)y + (uint32_t)g.ny * (uint32_t)z);
+    const uint32_t t = (uint32_t)tx + (uint32_t)g.nx * ((uint32_t)ty + (uint32_t)g.ny * (uint32_t)tz);
+    return {pidx(0, i, s), pidx(0, vel_opp(i), t)};
+}
+
 // Site indices of the pull sources x - c_i for the 19 velocities.
 struct PullIdx {
     int own;

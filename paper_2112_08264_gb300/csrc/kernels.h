@@ -28,9 +28,21 @@ struct AsyncPlan {
 // whose neighbour x + c_i is solid, in segment [off[i], off[i + 1]) of
 // `sites` (grouped by blocks of 256 consecutive sites, ascending within a
 // warp). sites == nullptr: no list (the copy pass scans every site).
+//
+// Links that stay inside one tile of the box kernel (same 32-column strip,
+// same row band, target plane inside the same z-chunk) are instead grouped
+// by (tile, source plane) for that kernel's tiling: list (b, z) is
+// tent[tstart[b nz + z], tstart[b nz + z + 1]), one LinkTiles entry per link.
+// The box kernel copies them itself while both ends are still in L2; any
+// other step kernel runs them as a separate pass. `sites` then holds only the
+// remaining links. tent == nullptr: no tile lists (`sites` holds every link).
 struct LinkList {
     const uint32_t* sites = nullptr;
     long long off[Q + 1] = {};
+    LinkTiles tiles;
+    TileMap map;              // the tiling the lists were built for
+    long long tmost = 0;      // longest (tile, plane) list
+    long long tcount = 0;     // links in the tile lists
 };
 
 struct StepLaunch {
@@ -60,18 +72,30 @@ cudaError_t launch_fused_async(const StepLaunch& L, cudaStream_t st);
 // Solid flags from a device mask (1 = solid).
 cudaError_t launch_flags(const uint8_t* mask, uint32_t* flags, const Geom& g, cudaStream_t st);
 
-// Build the link list of a mask (flags) into `sites` (capacity entries) with
-// `cursor` (2Q device words of scratch); the host waits for the counts. On
-// return L.sites is set when the links fit, else left nullptr.
-cudaError_t build_links(const uint32_t* flags, uint32_t* sites, size_t capacity, uint32_t* cursor, const Geom& g,
+// Build the link lists of a mask (flags); the host waits for the counts.
+// Tile lists (map.R > 0): entries into tent (tcap entries), offsets into
+// tstart (map.ncols * map.R * nz + 1 words), per-list counters in tscratch
+// (as many words); skipped (L.tiles.tent left nullptr) when the in-tile
+// links exceed tcap. The remaining links go into `sites` (capacity entries)
+// with `cursor` (2Q words of scratch); L.sites stays nullptr when they do not
+// fit (the pass then scans every site, in-tile links included: a second copy
+// of a link writes the same value).
+cudaError_t build_links(const uint32_t* flags, uint32_t* sites, size_t capacity, uint32_t* cursor, TileMap map,
+                        uint16_t* tent, size_t tcap, uint32_t* tstart, uint32_t* tscratch, const Geom& g,
                         LinkList& L, cudaStream_t st);
+
+// True when a step launched with L runs the tile lists inside its kernel
+// (the box kernel of the tiling the lists were built for).
+bool tiles_in_kernel(const StepLaunch& L);
 
 // Write-side halfway bounce-back on a freshly written state g: for every fluid
 // node x and direction i with x + c_i solid, copy g_i(x) into slot opp(i) of
 // x + c_i. The next pull of population opp(i) at x, from x - c_opp(i) = x + c_i,
 // then reads the bounced value without a mask test. Run after every masked step.
-cudaError_t launch_reflect(int prec, void* g_state, const uint32_t* flags, const LinkList& links, const Geom& g,
-                           cudaStream_t st);
+// With tile lists, `with_tiles` says whether this pass also copies them
+// (false when the step kernel already did).
+cudaError_t launch_reflect(int prec, void* g_state, const uint32_t* flags, const LinkList& links, bool with_tiles,
+                           const Geom& g, cudaStream_t st);
 
 // Internal state from a post-streaming population field: either the
 // equilibrium of (rhoA, rhoB, u) (f == nullptr) or the given f (float,

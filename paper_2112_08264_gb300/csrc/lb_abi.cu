@@ -4,6 +4,7 @@
 // workspace into the two population buffers of the one-step two-grid scheme
 // (Sec. 3), the solid mask and flags, density scratch, reduction scratch and,
 // when recording for the adjoint, the checkpoints and adjoint buffers.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -39,7 +40,7 @@ namespace {
 size_t store_bytes(int prec) { return prec == LB_FP32 ? 4 : 2; }
 
 struct Layout {
-    size_t pop[2], mask, flags, links, cursor, rho, red_part, red_out;
+    size_t pop[2], mask, flags, links, tent, tstart, cursor, rho, red_part, red_out;
     size_t ckpt, ckpt_slots, seg, adj;
     size_t state_bytes;
     size_t total;
@@ -82,6 +83,9 @@ Layout make_layout(int nx, int ny, int nz, const lb_options& o) {
     L.mask = off; off += align256(N);
     L.flags = off; off += align256(N * 4);
     L.links = off; off += align256(N * 4);   // bounce-back link list (masked grids), up to N links
+    L.tent = off; off += align256(N * 2);    // in-tile links grouped by (tile, plane), up to N
+    // list offsets: at most one tile per 32-column strip and row, per plane
+    L.tstart = off; off += align256((((size_t)nx + 31) / 32 * ny * nz + 1) * 4);
     L.cursor = off; off += align256(2 * Q * 4);
     L.rho = off; off += align256(2 * N * 4);
     L.red_part = off; off += align256((size_t)kRedBlocks * kRedVals * 8);
@@ -239,9 +243,19 @@ lb_status lb_create(int nx, int ny, int nz, float tau, float G, const uint8_t* m
     if (mask) {
         e = cudaMemcpyAsync(c->mask_dev, mask, (size_t)c->g.N, cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess) e = launch_flags(c->mask_dev, c->flags, c->g, c->stream);
+        // tile lists for the box kernel's tiling (counters in the density scratch)
+        TileMap map;
+        if (c->plan.box && c->plan.R > 0) {
+            map.ncols = c->plan.ncols;
+            map.R = c->plan.R;
+            map.zchunk = c->plan.zchunk;
+        }
         if (e == cudaSuccess)
             e = build_links(c->flags, reinterpret_cast<uint32_t*>(c->ws + L.links), (size_t)c->g.N,
-                            reinterpret_cast<uint32_t*>(c->ws + L.cursor), c->g, c->links, c->stream);
+                            reinterpret_cast<uint32_t*>(c->ws + L.cursor), map,
+                            reinterpret_cast<uint16_t*>(c->ws + L.tent), (size_t)c->g.N,
+                            reinterpret_cast<uint32_t*>(c->ws + L.tstart), reinterpret_cast<uint32_t*>(c->rho), c->g,
+                            c->links, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) {
             delete c;
@@ -282,11 +296,8 @@ lb_status lb_init(lb_ctx* c, const float* rA, const float* rB, const float* u) {
     return LB_OK;
 }
 
-lb_status lb_step(lb_ctx* c, int n) {
-    if (!c || n < 1) return LB_EINVAL;
-    if (!c->initialized) return LB_ESTATE;
-    const int K = c->opt.ckpt_every;
-    if (K > 0 && c->recording && c->steps + n > c->opt.ckpt_steps_max) return LB_ESTATE;
+namespace {
+StepLaunch step_launch(const lb_ctx* c) {
     StepLaunch S;
     S.prec = c->opt.prec;
     S.kernel = c->opt.kernel;
@@ -298,6 +309,27 @@ lb_status lb_step(lb_ctx* c, int n) {
     S.zsplit = c->zsplit;
     S.plan = c->plan;
     S.links = c->links;
+    return S;
+}
+
+// launches of the bounce-back passes after a masked step kernel
+int reflect_launches(const lb_ctx* c) {
+    if (!c->has_mask) return 0;
+    const LinkList& L = c->links;
+    if (!L.sites) return 1;   // the pass scans every site
+    long long most = 0;
+    for (int i = 1; i < Q; ++i) most = std::max(most, L.off[i + 1] - L.off[i]);
+    const bool tile_pass = L.tiles.ent && L.tmost > 0 && !tiles_in_kernel(step_launch(c));
+    return (most > 0 ? 1 : 0) + (tile_pass ? 1 : 0);
+}
+}  // namespace
+
+lb_status lb_step(lb_ctx* c, int n) {
+    if (!c || n < 1) return LB_EINVAL;
+    if (!c->initialized) return LB_ESTATE;
+    const int K = c->opt.ckpt_every;
+    if (K > 0 && c->recording && c->steps + n > c->opt.ckpt_steps_max) return LB_ESTATE;
+    StepLaunch S = step_launch(c);
     for (int t = 0; t < n; ++t) {
         S.src = c->pop[c->cur];
         S.dst = c->pop[1 - c->cur];
@@ -386,13 +418,22 @@ lb_status lb_backward(lb_ctx* c, const float* dLA, const float* dLB, float* gA, 
 lb_status lb_launch_info(const lb_ctx* c, int* launches, int* blocks, int* threads, int* zsplit) {
     if (!c) return LB_EINVAL;
     const int k = c->opt.kernel;
-    // a masked step adds the write-side bounce-back pass (launch_reflect)
-    if (launches) *launches = (k == LB_KERNEL_TWO_PASS ? 2 : 1) + (c->has_mask ? 1 : 0);
+    // a masked step adds the write-side bounce-back passes (launch_reflect)
+    if (launches) *launches = (k == LB_KERNEL_TWO_PASS ? 2 : 1) + reflect_launches(c);
     if (blocks)
         *blocks = k == LB_KERNEL_FUSED ? c->plan.ncols * c->plan.R * c->plan.zsplit
                 : k == LB_KERNEL_FUSED_REG ? c->tiles * c->zsplit : (int)((c->g.N + 255) / 256);
     if (threads) *threads = k == LB_KERNEL_FUSED ? c->plan.threads : k == LB_KERNEL_FUSED_REG ? c->threads : 256;
     if (zsplit) *zsplit = k == LB_KERNEL_FUSED ? c->plan.zsplit : c->zsplit;
+    return LB_OK;
+}
+
+lb_status lb_link_info(const lb_ctx* c, long long* listed, long long* in_tile, int* in_kernel) {
+    if (!c) return LB_EINVAL;
+    const LinkList& L = c->links;
+    if (listed) *listed = !c->has_mask ? 0 : (L.sites ? L.off[Q] : -1);
+    if (in_tile) *in_tile = L.tiles.ent ? L.tcount : 0;
+    if (in_kernel) *in_kernel = c->has_mask && tiles_in_kernel(step_launch(c)) ? 1 : 0;
     return LB_OK;
 }
 

@@ -2,6 +2,7 @@
 // (equilibrium, Eq. LEQ) and state import/export, moments, and the FP64
 // conservation reduction.
 #include <algorithm>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -16,6 +17,23 @@ __device__ __forceinline__ void site_xyz(long long s, const Geom& g, int& x, int
     x = (int)(s % g.nx);
     y = (int)((s / g.nx) % g.ny);
     z = (int)(s / g.plane);
+}
+
+// Is link (x, i) -- fluid node (x, y, z), solid target x + c_i -- inside one
+// tile of M: the target in the same column strip and row band (periodic in x
+// and y), its plane inside the source's z-chunk? Never when M.R == 0.
+template <int i>
+__device__ __forceinline__ bool in_tile(int x, int y, int z, const Geom& g, const TileMap& M) {
+    if (M.R == 0) return false;
+    const int za = (z / M.zchunk) * M.zchunk;
+    const int tz = z + Vel<i>::z;
+    if (tz < za || tz >= min(za + M.zchunk, g.nz)) return false;
+    const int tx = Vel<i>::x > 0 ? wrap_inc(x, g.nx) : (Vel<i>::x < 0 ? wrap_dec(x, g.nx) : x);
+    const int ty = Vel<i>::y > 0 ? wrap_inc(y, g.ny) : (Vel<i>::y < 0 ? wrap_dec(y, g.ny) : y);
+    return tx / kTileX == x / kTileX && band_of(ty, g.ny, M.R) == band_of(y, g.ny, M.R);
+}
+__device__ __forceinline__ int tile_index(int x, int y, const Geom& g, const TileMap& M) {
+    return x / kTileX + M.ncols * band_of(y, g.ny, M.R);
 }
 
 __global__ void flags_kernel(const uint8_t* __restrict__ mask, uint32_t* __restrict__ flags, Geom g) {
@@ -66,16 +84,20 @@ __global__ void reflect_kernel(const S* __restrict__ in, S* __restrict__ out,
 // Link list, pass 1: per velocity, the number of fluid sites x with x + c_i
 // solid (flag bit opp(i)); block totals in shared memory, one global atomic
 // per velocity and block.
-__global__ void link_count_kernel(const uint32_t* __restrict__ flags, uint32_t* __restrict__ counts, Geom g) {
+__global__ void link_count_kernel(const uint32_t* __restrict__ flags, uint32_t* __restrict__ counts, TileMap M,
+                                  Geom g) {
     __shared__ uint32_t cnt[Q];
     if (threadIdx.x < Q) cnt[threadIdx.x] = 0u;
     __syncthreads();
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t fl = s < g.N ? __ldg(flags + s) : kSolid;
     const bool fluid = !(fl & kSolid);
+    int x = 0, y = 0, z = 0;
+    if (s < g.N) site_xyz(s, g, x, y, z);
     static_for<1, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        const unsigned b = __ballot_sync(0xffffffffu, fluid && (fl & (1u << Vel<i>::opp)));
+        const unsigned b = __ballot_sync(0xffffffffu, fluid && (fl & (1u << Vel<i>::opp)) &&
+                                                          !in_tile<i>(x, y, z, g, M));
         if ((threadIdx.x & 31) == 0 && b) atomicAdd(&cnt[i], (uint32_t)__popc(b));
     });
     __syncthreads();
@@ -86,19 +108,24 @@ __global__ void link_count_kernel(const uint32_t* __restrict__ flags, uint32_t* 
 // segment with one atomic, warps take consecutive parts of it, lanes their
 // rank within the warp.
 __global__ void link_fill_kernel(const uint32_t* __restrict__ flags, uint32_t* __restrict__ cursor,
-                                 uint32_t* __restrict__ sites, LinkList L, Geom g) {
+                                 uint32_t* __restrict__ sites, LinkList L, TileMap M, Geom g) {
     __shared__ uint32_t cnt[Q], base[Q];
     if (threadIdx.x < Q) cnt[threadIdx.x] = 0u;
     __syncthreads();
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t fl = s < g.N ? __ldg(flags + s) : kSolid;
     const bool fluid = !(fl & kSolid);
+    int x = 0, y = 0, z = 0;
+    if (s < g.N) site_xyz(s, g, x, y, z);
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     uint32_t wpos[Q];
+    uint32_t mine = 0u;   // this node's links that go into `sites`
     static_for<1, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        const unsigned b = __ballot_sync(0xffffffffu, fluid && (fl & (1u << Vel<i>::opp)));
+        const bool own = fluid && (fl & (1u << Vel<i>::opp)) && !in_tile<i>(x, y, z, g, M);
+        mine |= own ? (1u << i) : 0u;
+        const unsigned b = __ballot_sync(0xffffffffu, own);
         uint32_t w = 0u;
         if (lane == 0 && b) w = atomicAdd(&cnt[i], (uint32_t)__popc(b));
         wpos[i] = __shfl_sync(0xffffffffu, w, 0) + (uint32_t)__popc(b & lt);
@@ -109,8 +136,68 @@ __global__ void link_fill_kernel(const uint32_t* __restrict__ flags, uint32_t* _
     __syncthreads();
     static_for<1, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        if (fluid && (fl & (1u << Vel<i>::opp))) sites[L.off[i] + base[i] + wpos[i]] = (uint32_t)s;
+        if (mine & (1u << i)) sites[L.off[i] + base[i] + wpos[i]] = (uint32_t)s;
     });
+}
+
+// Tile lists, pass 1: per (tile, plane) the number of in-tile links of the
+// fluid nodes there (all links of a node share its tile).
+__global__ void tile_count_kernel(const uint32_t* __restrict__ flags, uint32_t* __restrict__ counts, TileMap M,
+                                  Geom g) {
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.N) return;
+    const uint32_t fl = __ldg(flags + s);
+    if ((fl & kSolid) || !(fl & kNbSolidMask)) return;
+    int x, y, z;
+    site_xyz(s, g, x, y, z);
+    uint32_t n = 0u;
+    static_for<1, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        if ((fl & (1u << Vel<i>::opp)) && in_tile<i>(x, y, z, g, M)) ++n;
+    });
+    if (n) atomicAdd(&counts[(size_t)tile_index(x, y, g, M) * g.nz + z], n);
+}
+
+// Tile lists, pass 2: each node reserves its links' places in its list with
+// one atomic (the order within a list is immaterial: links are independent).
+__global__ void tile_fill_kernel(const uint32_t* __restrict__ flags, uint32_t* __restrict__ cursor,
+                                 const uint32_t* __restrict__ start, uint16_t* __restrict__ ent, TileMap M,
+                                 Geom g) {
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.N) return;
+    const uint32_t fl = __ldg(flags + s);
+    if ((fl & kSolid) || !(fl & kNbSolidMask)) return;
+    int x, y, z;
+    site_xyz(s, g, x, y, z);
+    uint32_t n = 0u;
+    static_for<1, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        if ((fl & (1u << Vel<i>::opp)) && in_tile<i>(x, y, z, g, M)) ++n;
+    });
+    if (!n) return;
+    const size_t list = (size_t)tile_index(x, y, g, M) * g.nz + z;
+    uint32_t pos = start[list] + atomicAdd(&cursor[list], n);
+    const int lx = x % kTileX, ly = y - band_start(band_of(y, g.ny, M.R), g.ny, M.R);
+    static_for<1, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        if ((fl & (1u << Vel<i>::opp)) && in_tile<i>(x, y, z, g, M)) ent[pos++] = link_entry(lx, ly, i);
+    });
+}
+
+// The tile lists as a pass of their own (step kernels other than the box
+// kernel): one block per (tile, plane) list.
+template <typename S>
+__global__ void reflect_tiles_kernel(const S* __restrict__ in, S* __restrict__ out, LinkTiles T, TileMap M,
+                                     Geom g) {
+    using P = typename Store<S>::Pair;
+    const long long b = blockIdx.x;
+    const uint32_t a = __ldg(T.start + b), e = __ldg(T.start + b + 1);
+    const int tile = (int)(b / g.nz), z = (int)(b - (long long)tile * g.nz);
+    const int x0 = (tile % M.ncols) * kTileX, y0 = band_start(tile / M.ncols, g.ny, M.R);
+    for (uint32_t k = a + threadIdx.x; k < e; k += blockDim.x) {
+        const LinkSlots ls = tile_link_slots(__ldg(T.ent + k), x0, y0, z, g);
+        *reinterpret_cast<P*>(out + ls.dst) = __ldg(reinterpret_cast<const P*>(in + ls.src));
+    }
 }
 
 // The copy pass over the links: block row blockIdx.y + 1 = velocity i; one
@@ -362,33 +449,83 @@ cudaError_t launch_flags(const uint8_t* mask, uint32_t* flags, const Geom& g, cu
     return cudaGetLastError();
 }
 
-cudaError_t build_links(const uint32_t* flags, uint32_t* sites, size_t capacity, uint32_t* cursor, const Geom& g,
+cudaError_t build_links(const uint32_t* flags, uint32_t* sites, size_t capacity, uint32_t* cursor, TileMap M,
+                        uint16_t* tent, size_t tcap, uint32_t* tstart, uint32_t* tscratch, const Geom& g,
                         LinkList& L, cudaStream_t st) {
     L = LinkList{};
     const unsigned nb = blocks_for(g.N, 256);
-    cudaError_t e = cudaMemsetAsync(cursor, 0, 2 * Q * sizeof(uint32_t), st);
-    if (e != cudaSuccess) return e;
-    link_count_kernel<<<nb, 256, 0, st>>>(flags, cursor, g);
+    cudaError_t e = cudaSuccess;
+    LinkList T;
+    if (M.R > 0 && tent && tstart && tscratch) {
+        const size_t lists = (size_t)M.ncols * M.R * g.nz;
+        if ((e = cudaMemsetAsync(tscratch, 0, lists * sizeof(uint32_t), st)) != cudaSuccess) return e;
+        tile_count_kernel<<<nb, 256, 0, st>>>(flags, tscratch, M, g);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        std::vector<uint32_t> off(lists + 1);
+        if ((e = cudaMemcpyAsync(off.data(), tscratch, lists * sizeof(uint32_t), cudaMemcpyDeviceToHost, st)) !=
+            cudaSuccess)
+            return e;
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+        unsigned long long run = 0;
+        long long most = 0;
+        for (size_t k = 0; k < lists; ++k) {
+            const uint32_t n = off[k];
+            off[k] = (uint32_t)run;
+            run += n;
+            most = std::max(most, (long long)n);
+        }
+        if (run <= tcap && run < (1ull << 32)) {
+            off[lists] = (uint32_t)run;
+            if ((e = cudaMemcpyAsync(tstart, off.data(), (lists + 1) * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                                     st)) != cudaSuccess)
+                return e;
+            if ((e = cudaMemsetAsync(tscratch, 0, lists * sizeof(uint32_t), st)) != cudaSuccess) return e;
+            tile_fill_kernel<<<nb, 256, 0, st>>>(flags, tscratch, tstart, tent, M, g);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            // the host copy of the offsets must outlive the upload
+            if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+            T.tiles.start = tstart;
+            T.tiles.ent = tent;
+            T.map = M;
+            T.tmost = most;
+            T.tcount = (long long)run;
+        }
+    }
+    const TileMap R = T.tiles.ent ? T.map : TileMap{};
+    if ((e = cudaMemsetAsync(cursor, 0, 2 * Q * sizeof(uint32_t), st)) != cudaSuccess) return e;
+    link_count_kernel<<<nb, 256, 0, st>>>(flags, cursor, R, g);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     uint32_t counts[Q];
     if ((e = cudaMemcpyAsync(counts, cursor, Q * sizeof(uint32_t), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return e;
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
-    LinkList T;
     T.off[0] = T.off[1] = 0;
     for (int i = 1; i < Q; ++i) T.off[i + 1] = T.off[i] + counts[i];
-    if ((size_t)T.off[Q] > capacity) return cudaSuccess;   // too many links: the pass scans every site
+    if ((size_t)T.off[Q] > capacity) {   // too many links: the pass scans every site (tile lists unused)
+        L = LinkList{};
+        return cudaSuccess;
+    }
     T.sites = sites;
     if ((e = cudaMemsetAsync(cursor + Q, 0, Q * sizeof(uint32_t), st)) != cudaSuccess) return e;
-    link_fill_kernel<<<nb, 256, 0, st>>>(flags, cursor + Q, sites, T, g);
+    link_fill_kernel<<<nb, 256, 0, st>>>(flags, cursor + Q, sites, T, R, g);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     L = T;
     return cudaStreamSynchronize(st);
 }
 
-cudaError_t launch_reflect(int prec, void* g_state, const uint32_t* flags, const LinkList& links, const Geom& g,
-                           cudaStream_t st) {
+cudaError_t launch_reflect(int prec, void* g_state, const uint32_t* flags, const LinkList& links, bool with_tiles,
+                           const Geom& g, cudaStream_t st) {
     if (links.sites) {
+        if (links.tiles.ent && with_tiles && links.tmost > 0) {
+            const unsigned lists = (unsigned)((long long)links.map.ncols * links.map.R * g.nz);
+#define LBGB_TILES(T)                                                                                            \
+    [&] {                                                                                                        \
+        reflect_tiles_kernel<T><<<lists, 128, 0, st>>>((const T*)g_state, (T*)g_state, links.tiles, links.map, g); \
+    }
+            const cudaError_t e = by_prec(prec, LBGB_TILES(float), LBGB_TILES(__half), LBGB_TILES(__nv_bfloat16));
+#undef LBGB_TILES
+            if (e != cudaSuccess) return e;
+        }
         long long most = 0;
         for (int i = 1; i < Q; ++i) most = std::max(most, links.off[i + 1] - links.off[i]);
         if (most == 0) return cudaSuccess;

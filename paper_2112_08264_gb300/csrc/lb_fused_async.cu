@@ -29,6 +29,7 @@ namespace lbgb {
 namespace {
 
 constexpr int kTX = 32;
+static_assert(kTX == kTileX, "the bounce-back tile lists assume the box kernel's strip width");
 constexpr int kMaxTY = 16;
 
 __device__ __forceinline__ int wrap_any(int a, int n) {
@@ -236,7 +237,7 @@ __device__ __forceinline__ void cp_async16(uint32_t saddr, const void* gptr) {
 template <typename S, bool MASK, int MODEL = 0>
 __global__ void __launch_bounds__(kTX * kMaxTY, 1)
 fused_box_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t* __restrict__ flags,
-                 float* __restrict__ mom_out, Geom g, Phys p, AsyncPlan P) {
+                 float* __restrict__ mom_out, Geom g, Phys p, AsyncPlan P, LinkTiles LT) {
     constexpr bool CG = MODEL == 1;
     // what a node contributes to the ring: its density deviations, or Theta
     auto ring_val = [&](float2 d) -> float2 {
@@ -286,6 +287,41 @@ fused_box_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t*
     const int hgx = wrap_any(x0 + hlx, g.nx), hgy = wrap_any(y0 + hly, g.ny);
 
     auto plane_of = [&](int e) { return wrap_any(z0 - 1 + e, g.nz); };
+
+    // In-tile bounce-back links (masked Shan-Chen grids): the links whose
+    // source node lies in plane z0 + e - 3 are copied across two events --
+    // event e fetches the entry after its first barrier and loads the source
+    // slot after its collision; event e + 1 stores the target slot, after its
+    // second barrier (FP32) or after its collision (16-bit storage; each
+    // placement measured faster for its precision). By then every plane they
+    // touch (z - 1, z, z + 1 of the tile, inside this z-chunk) was written by
+    // this block before a barrier, and both slots are recent writes still in
+    // L2. Thread t takes entry t of a list; a longer list's rest is copied in
+    // one go at the store point. The list offsets of planes z0 .. z1 sit
+    // after the ring.
+    using LP = typename Store<S>::Pair;
+    constexpr bool kLinks = MASK && MODEL == 0;
+    constexpr bool kLateStore = sizeof(S) == 2;
+    const bool links = kLinks && LT.ent != nullptr;
+    uint32_t* lstart = reinterpret_cast<uint32_t*>(ring + 4 * RH * RW);
+    if (links)
+        for (int k = t; k <= z1 - z0; k += P.threads) lstart[k] = __ldg(LT.start + (size_t)blockIdx.x * g.nz + z0 + k);
+    // the links of list plane zl beyond the first P.threads, or all from k0 on
+    auto copy_links = [&](int zl, uint32_t k0) {
+        const uint32_t a = lstart[zl], n = lstart[zl + 1] - a;
+        for (uint32_t k = k0; k < n; k += (uint32_t)P.threads) {
+            const LinkSlots ls = tile_link_slots(__ldg(LT.ent + a + k), x0, y0, z0 + zl, g);
+            *reinterpret_cast<LP*>(dst + ls.dst) = __ldcg(reinterpret_cast<const LP*>(dst + ls.src));
+        }
+    };
+    uint32_t lent = 0u, lent_p = 0u;
+    bool lhave = false, lhave_p = false;
+    LP lval{};
+    // targets of list plane zl, whose sources were loaded one event earlier
+    auto store_links = [&](int zl) {
+        if (lhave_p) *reinterpret_cast<LP*>(dst + tile_link_slots(lent_p, x0, y0, z0 + zl, g).dst) = lval;
+        copy_links(zl, (uint32_t)(t + P.threads));
+    };
 
     // Copier thread t (< RH * CPR) owns chunk (row jr, column jc) of all 19
     // boxes. Its wrapped source offsets within a plane depend only on c_iy
@@ -413,6 +449,11 @@ fused_box_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t*
         cp_wait_n(ahead - 1);
         __syncthreads();   // every thread's chunks of event e are visible
         if constexpr (early) issue(e + ahead, z_iss, st_cur == 0 ? P.nst - 1 : st_cur - 1);
+        if (kLinks && links && e >= 3) {   // entry of plane z0 + e - 3, used after the collision
+            const uint32_t a = lstart[e - 3];
+            lhave = (uint32_t)t < lstart[e - 2] - a;
+            if (lhave) lent = __ldg(LT.ent + a + t);
+        }
         const int slot = e & 3;
         nxt.fl = kSolid;
         if (own_row) {
@@ -430,6 +471,7 @@ fused_box_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t*
         }
         __syncthreads();   // ring of plane e complete; stage st_cur fully read
         if constexpr (!early) issue(e + ahead, z_iss, st_cur);
+        if (kLinks && !kLateStore && links && e >= 4) store_links(e - 4);
         PlaneSums ps_hi;
         if constexpr (packed) {
             const float2* rn = ring + slot * RH * RW + own_off;
@@ -492,6 +534,12 @@ fused_box_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t*
                     collide_store<S, MASK>(cur.d, p, dA, dB, j, SA, SB, dst, g, (int)own, solid);
             }
         }
+        if (kLinks && kLateStore && links && e >= 4) store_links(e - 4);
+        if (kLinks && links && e >= 3) {   // sources of plane z0 + e - 3
+            lhave_p = lhave;
+            lent_p = lent;
+            if (lhave) lval = __ldcg(reinterpret_cast<const LP*>(dst + tile_link_slots(lent, x0, y0, z0 + e - 3, g).src));
+        }
         if constexpr (packed) {
             ps_lo = ps_mid;
             ps_mid = ps_hi;
@@ -506,6 +554,11 @@ fused_box_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t*
         if (e + 1 < L) event(e + 1, h1, h0);
     }
     cp_wait<0>();
+    if (kLinks && links) {
+        __syncthreads();   // the last plane's stores are visible to the block
+        if (L >= 4) store_links(L - 4);   // plane z1 - 2: sources loaded after the last collision
+        copy_links(L - 3, (uint32_t)t);   // plane z1 - 1
+    }
 }
 
 template <typename S, bool MASK, int MODEL = 0>
@@ -519,8 +572,9 @@ cudaError_t launch_box_t(const StepLaunch& L, cudaStream_t st) {
         configured = P.smem;
     }
     dim3 grid(P.ncols * P.R, P.zsplit, 1);
+    const LinkTiles lt = tiles_in_kernel(L) ? L.links.tiles : LinkTiles{};
     kern<<<grid, P.threads, P.smem, st>>>(static_cast<const S*>(L.src), static_cast<S*>(L.dst), L.flags, L.mom_out,
-                                          L.g, L.p, P);
+                                          L.g, L.p, P, lt);
     return cudaGetLastError();
 }
 
@@ -588,13 +642,15 @@ AsyncPlan plan_fused_async(int nx, int ny, int nz, int sm_count, int prec, bool 
         const size_t stage = box ? (size_t)(tymax + 2) * row_bytes + (masked ? (size_t)(tymax + 2) * 40 * 4 : 0)
                                  : (size_t)Q * ns * 2 * esize + (masked ? (size_t)ns * 4 : 0);
         const size_t ring = (size_t)4 * (tymax + 2) * (kTX + 2) * 8;
-        if (smem_limit < ring + 2 * stage) continue;
-        int nst = (int)((smem_limit - ring) / stage);
-        nst = nst > 4 ? 4 : nst;
         const long long bxy = (long long)ncols * R;
         const int zs_max = nz / 4 > 1 ? nz / 4 : 1;
         for (int zs = 1; zs <= zs_max; ++zs) {
             const int zchunk = (nz + zs - 1) / zs;
+            // masked box kernel: the bounce-back list offsets of the chunk's planes
+            const size_t lists = masked && box ? ((size_t)(zchunk + 1) * 4 + 15) / 16 * 16 : 0;
+            if (smem_limit < ring + lists + 2 * stage) continue;
+            int nst = (int)((smem_limit - ring - lists) / stage);
+            nst = nst > 4 ? 4 : nst;
             const long long blocks = bxy * zs;
             const long long waves = (blocks + sm_count - 1) / sm_count;
             // per-block time ~ columns (own + 30% weight for halo nodes) x planes
@@ -611,7 +667,7 @@ AsyncPlan plan_fused_async(int nx, int ny, int nz, int sm_count, int prec, bool 
                 best.nst = nst;
                 best.threads = threads;
                 best.ns = ns;
-                best.smem = ring + (size_t)nst * stage;
+                best.smem = ring + lists + (size_t)nst * stage;
                 best.box = box ? 1 : 0;
             }
             if (blocks >= sm_count) break;   // more z-splits only add halo planes

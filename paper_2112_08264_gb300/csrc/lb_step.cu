@@ -221,10 +221,16 @@ cudaError_t launch_step_kernels(const StepLaunch& L, cudaStream_t st) {
 }
 }  // namespace
 
+bool tiles_in_kernel(const StepLaunch& L) {
+    const LinkList& k = L.links;
+    return L.flags != nullptr && k.sites != nullptr && k.tiles.ent != nullptr && L.kernel == 0 && L.p.model == 0 &&
+           L.plan.box && k.map.ncols == L.plan.ncols && k.map.R == L.plan.R && k.map.zchunk == L.plan.zchunk;
+}
+
 cudaError_t launch_step(const StepLaunch& L, cudaStream_t st) {
     const cudaError_t e = launch_step_kernels(L, st);
     if (e != cudaSuccess || L.flags == nullptr) return e;
-    return launch_reflect(L.prec, L.dst, L.flags, L.links, L.g, st);
+    return launch_reflect(L.prec, L.dst, L.flags, L.links, !tiles_in_kernel(L), L.g, st);
 }
 
 void fused_geometry(int nx, int ny, int nz, int sm_count, int* tiles, int* zsplit, int* threads) {

@@ -148,6 +148,15 @@ class Solver:
         return {"launches_per_step": v[0].value, "grid_blocks": v[1].value,
                 "block_threads": v[2].value, "z_split": v[3].value}
 
+    def link_info(self):
+        """Bounce-back links of the mask: ``listed`` in the per-velocity pass
+        (-1: the pass scans every site), ``in_tile`` grouped by step-kernel
+        tile, ``in_kernel`` whether the step kernel copies those itself."""
+        a, b, k = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_int()
+        _lib.check(_lib.lib().lb_link_info(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(k)),
+                   "lb_link_info")
+        return {"listed": a.value, "in_tile": b.value, "in_kernel": bool(k.value)}
+
 
 def create(nx, ny, nz, tau, G, mask=None, **kw):
     """``lb_create(nx, ny, nz, tau, G, mask)`` in Python form."""
