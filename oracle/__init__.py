@@ -18,6 +18,9 @@ Three independent formulations live here:
   derivatives for the adjoint checks.
 * ``single_bgk``: one-component D3Q19 BGK, which the two-component step must
   reduce to at G = 0.
+* ``particles``: moving rigid spheres (moving-wall bounce-back, link forces
+  and torques, leap-frog, re-meshing) on the write-side state the library
+  holds.
 
 Arrays: populations ``f`` have shape ``(2, 19, nz, ny, nx)`` (component,
 velocity in the library's public order, z, y, x), fields ``(nz, ny, nx)``,

@@ -1,0 +1,294 @@
+"""Moving rigid spheres coupled to the two-component step, FP64 numpy.
+
+TEST INFRASTRUCTURE (see the package docstring): only tests and the
+benchmark's CPU legs use it; the library never imports it.
+
+Model (Sec. 2): each particle p is a rigid sphere of radius R with centre
+r_p, velocity v_p and angular velocity w_p; a node x is covered by p when its
+periodic (minimum-image) distance to r_p is at most R. Only the exterior
+holds fluid (the Jansen-Harting form the paper adopts): covered nodes carry
+no populations. Per step, in this order:
+
+1. Links and forces. For every fluid node x and direction i whose neighbour
+   x + c_i is covered by p, the wall sits at the link midpoint
+   r_b = x + c_i / 2 and moves with u_b = v_p + w_p x (r_b - r_p) (Eq. UPI);
+   the population g_i(x) leaving x returns to x as population opp(i) reduced
+   by 2 rho w_i (u_b . c_i) / c_s^2 (Eq. LADDFLBE), and the link passes the
+   momentum it exchanges with the fluid to the particle (Eq. FORCEPP, summed
+   over links in Eq. FORCEPARTEQ and Eq. TORQUEPARTEQ with the arm r_b - r_p).
+2. The fluid step: streaming (pull) and the Shan-Chen BGK collision, with
+   psi = 0 on every solid node.
+3. Newton's equations (Eq. PARDYN) by leap-frog: v += F / m, r += v,
+   w += T / I, with I = 2 m R^2 / 5 (a uniform sphere); m <= 0 marks a fixed
+   particle (its force and torque are still computed).
+4. Re-meshing: nodes the moved sphere no longer covers become fluid with the
+   equilibrium populations of density rho0^k and the local wall velocity;
+   nodes it newly covers lose their fluid. The particle takes up the
+   momentum (and its moment) that the fluid gains or loses there, so the
+   total momentum of fluid and particles is unchanged.
+
+Readings where the paper is silent (listed with the design notes):
+* rho in the bias of Eq. LADDFLBE is each component's base density rho0^k;
+* Eq. FORCEPP subtracts the populations of fluid inside the particle (Ladd's
+  form), but under the exterior-only form the paper adopts there is none:
+  the link force here is the momentum the bounce exchanges with the
+  exterior fluid, c_i sum_k (2 g_i^k(x) - 2 rho0^k w_i (u_b . c_i) / c_s^2);
+* the re-meshing rule (item 4) is not given in the paper; it is chosen to
+  conserve momentum exactly.
+
+State (the library's write-side representation): g holds the post-collision
+populations at fluid nodes and, at solid nodes, the slots the next pull
+reads (slot opp(i) of solid y = x + c_i holds the bounced population of
+fluid x). Arrays use ``lb_numpy``'s velocity order (``VEL``), shape
+(2, 19, nz, ny, nx); ``post_streaming`` gives the pulled populations in that
+order.
+"""
+import numpy as np
+
+from . import lb_numpy as ln
+
+VEL = ln.VEL
+W = ln.W
+OPP = ln.OPP
+CS2 = ln.CS2
+
+
+def shift_from(a, c):
+    """Field whose value at x is a(x + c) (periodic; the last three axes are
+    z, y, x)."""
+    return np.roll(a, shift=(-int(c[2]), -int(c[1]), -int(c[0])), axis=(-3, -2, -1))
+
+
+def shift_to(a, c):
+    """Field whose value at x + c is a(x)."""
+    return np.roll(a, shift=(int(c[2]), int(c[1]), int(c[0])), axis=(-3, -2, -1))
+
+
+def min_image(d, n):
+    """Minimum-image displacement along one axis of period n."""
+    return d - n * np.round(d / n)
+
+
+def coverage(shape, r, radius):
+    """Per-node owner: -1 = not covered, p = covered by particle p (distance
+    to r_p at most radius, periodic). Overlapping particles are an error."""
+    nz, ny, nx = shape
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    owner = np.full(shape, -1, dtype=np.int64)
+    for p, c in enumerate(np.asarray(r, dtype=np.float64).reshape(-1, 3)):
+        dx = min_image(x - c[0], nx)
+        dy = min_image(y - c[1], ny)
+        dz = min_image(z - c[2], nz)
+        inside = dx * dx + dy * dy + dz * dz <= radius * radius
+        if np.any(owner[inside] >= 0):
+            raise ValueError("particles overlap")
+        owner[inside] = p
+    return owner
+
+
+class Particles:
+    """Rigid spheres: positions r, velocities v, angular velocities w (all
+    (P, 3) float64), a common radius and mass (mass <= 0: fixed)."""
+
+    def __init__(self, r, v=None, w=None, radius=5.0, mass=1.0):
+        self.r = np.array(r, dtype=np.float64).reshape(-1, 3)
+        P = len(self.r)
+        self.v = np.zeros((P, 3)) if v is None else np.array(v, dtype=np.float64).reshape(P, 3)
+        self.w = np.zeros((P, 3)) if w is None else np.array(w, dtype=np.float64).reshape(P, 3)
+        self.radius = float(radius)
+        self.mass = float(mass)
+        self.F = np.zeros((P, 3))
+        self.T = np.zeros((P, 3))
+
+    @property
+    def inertia(self):
+        return 0.4 * self.mass * self.radius ** 2
+
+    def copy(self):
+        c = Particles(self.r, self.v, self.w, self.radius, self.mass)
+        c.F, c.T = self.F.copy(), self.T.copy()
+        return c
+
+
+def _arm(shape, x, y, z, centre):
+    nz, ny, nx = shape
+    return np.stack([min_image(x - centre[0], nx), min_image(y - centre[1], ny), min_image(z - centre[2], nz)])
+
+
+def init(rhoA, rhoB, u, mask, owner):
+    """The state whose pull is the equilibrium f^eq(rho^k, u) at every fluid
+    node (0 on solid nodes): g_i(y) = f_i(y + c_i) where y + c_i is fluid,
+    g_i(y) = f_opp(i)(y) at a fluid y whose neighbour y + c_i is solid (the
+    bounce at rest), 0 elsewhere."""
+    solid = _solid(mask, owner)
+    f = ln.init(rhoA, rhoB, u, solid.astype(np.uint8))
+    fluid = ~solid
+    g = np.zeros_like(f)
+    for i, c in enumerate(VEL):
+        dest_fluid = shift_from(fluid, c)          # y + c_i fluid
+        g[:, i] = np.where(dest_fluid, shift_from(f[:, i], c), 0.0)
+        g[:, i] += np.where(fluid & ~dest_fluid, f[:, OPP[i]], 0.0)
+    return g
+
+
+def _solid(mask, owner):
+    s = owner >= 0
+    if mask is not None:
+        s = s | (np.asarray(mask) != 0)
+    return s
+
+
+def links_and_forces(g, owner, mask, parts, rho0):
+    """Step 1: write every solid slot a fluid node pulls (moving-wall bounce
+    at particle nodes, bounce at rest at static solid nodes) and return the
+    force and torque of every particle (FP64 sums over its links)."""
+    shape = g.shape[2:]
+    nz, ny, nx = shape
+    solid = _solid(mask, owner)
+    fluid = ~solid
+    static = np.zeros(shape, bool) if mask is None else (np.asarray(mask) != 0)
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    P = len(parts.r)
+    F = np.zeros((P, 3))
+    T = np.zeros((P, 3))
+    out = g.copy()
+    for i, c in enumerate(VEL):
+        if not c.any():
+            continue
+        o = OPP[i]
+        nb_owner = shift_from(owner, c)             # owner of x + c_i
+        nb_static = shift_from(static, c)
+        # static solid neighbour: the slot takes g_i(x) unchanged
+        at = fluid & nb_static
+        for k in range(2):
+            slot = np.where(at, g[k, i], 0.0)
+            out[k, o] = np.where(shift_to(at, c), shift_to(slot, c), out[k, o])
+        for p in range(P):
+            at = fluid & (nb_owner == p)
+            if not at.any():
+                continue
+            xs, ys, zs = x[at], y[at], z[at]
+            arm = _arm(shape, xs + 0.5 * c[0], ys + 0.5 * c[1], zs + 0.5 * c[2], parts.r[p])
+            ub = parts.v[p][:, None] + np.cross(parts.w[p], arm.T).T
+            cu = (c[:, None] * ub).sum(axis=0) / CS2
+            exch = np.zeros(len(xs))
+            tz, ty, tx = (zs + c[2]) % nz, (ys + c[1]) % ny, (xs + c[0]) % nx
+            for k in range(2):
+                gi = g[k, i][at]
+                bias = 2.0 * rho0[k] * W[i] * cu
+                out[k, o, tz, ty, tx] = gi - bias
+                exch += 2.0 * gi - bias
+            dF = c[:, None] * exch[None, :]
+            F[p] += dF.sum(axis=1)
+            T[p] += np.cross(arm.T, dF.T).sum(axis=0)
+    return out, F, T
+
+
+def pulled(g, owner, mask, parts, rho0):
+    """The post-streaming populations a state stands for: its solid slots
+    written (item 1, forces discarded), then pulled; 0 on solid nodes."""
+    f = post_streaming(links_and_forces(g, owner, mask, parts, rho0)[0])
+    return f * ~_solid(mask, owner)
+
+
+def post_streaming(g):
+    """Pull every node: f_i(x) = g_i(x - c_i) (solid sources are slots)."""
+    f = np.empty_like(g)
+    for i, c in enumerate(VEL):
+        f[:, i] = shift_to(g[:, i], c)
+    return f
+
+
+def collide(f, tau, G, gbody, solid):
+    """Step 2's collision at fluid nodes (Shan-Chen velocity shift and BGK,
+    psi = 0 on solid nodes); 0 on solid nodes."""
+    m = solid.astype(np.uint8)
+    f = f * (~solid)
+    fluid = (~solid).astype(np.float64)
+    rho, Fsc = ln.density_force(f, G, gbody, m)
+    mom = np.einsum("kiabc,id->dabc", f, VEL.astype(np.float64))
+    safe = lambda r: r + (1.0 - fluid)
+    up = (mom / tau) / safe(rho[0] / tau + rho[1] / tau)
+    out = np.empty_like(f)
+    for k in range(2):
+        ueq = up + tau * Fsc[k] / safe(rho[k])
+        out[k] = (f[k] - (f[k] - ln.equilibrium(rho[k], ueq)) / tau) * fluid
+    return out
+
+
+def advance(parts):
+    """Step 3: leap-frog with the force and torque of step 1."""
+    if parts.mass <= 0:
+        return
+    parts.v = parts.v + parts.F / parts.mass
+    parts.r = parts.r + parts.v
+    parts.w = parts.w + parts.T / parts.inertia
+
+
+def remesh(g, owner, mask, parts, rho0):
+    """Step 4 for moved particles: uncovered nodes first (all particles),
+    then newly covered ones; returns the new owner field. Each particle's
+    velocity takes the momentum change of its own nodes after each pass."""
+    shape = g.shape[2:]
+    nz, ny, nx = shape
+    for p in range(len(parts.r)):
+        parts.r[p] = np.mod(parts.r[p], (nx, ny, nz))
+    new = coverage(shape, parts.r, parts.radius)
+    static = np.zeros(shape, bool) if mask is None else (np.asarray(mask) != 0)
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    g = g.copy()
+    fixed = parts.mass <= 0
+    # uncovered: fluid at the wall velocity and rho0
+    for p in range(len(parts.r)):
+        at = (owner == p) & (new != p)
+        if not at.any():
+            continue
+        arm = _arm(shape, x[at], y[at], z[at], parts.r[p])
+        ub = parts.v[p][:, None] + np.cross(parts.w[p], arm.T).T
+        dP = np.zeros(3)
+        dL = np.zeros(3)
+        for k in range(2):
+            feq = ln.equilibrium(np.full(arm.shape[1], rho0[k]), ub)
+            g[k][:, at] = feq
+            dP -= rho0[k] * ub.sum(axis=1)
+            dL -= rho0[k] * np.cross(arm.T, ub.T).sum(axis=0)
+        if not fixed:
+            parts.v[p] += dP / parts.mass
+            parts.w[p] += dL / parts.inertia
+    owner_mid = np.where(owner >= 0, np.where(new == owner, owner, -1), -1)
+    # newly covered: the fluid there goes to the particle
+    for p in range(len(parts.r)):
+        at = (new == p) & (owner_mid != p)
+        if not at.any():
+            continue
+        if np.any(static[at]) or np.any(owner_mid[at] >= 0):
+            raise ValueError("a particle covers a solid node")
+        arm = _arm(shape, x[at], y[at], z[at], parts.r[p])
+        mom = np.einsum("kin,id->dn", g[:, :, at], VEL.astype(np.float64))
+        g[:, :, at] = 0.0
+        if not fixed:
+            parts.v[p] += mom.sum(axis=1) / parts.mass
+            parts.w[p] += np.cross(arm.T, mom.T).sum(axis=0) / parts.inertia
+    return g, new
+
+
+def step(g, owner, mask, parts, tau, G, rho0, gbody=None):
+    """One step (items 1-4); returns (g, owner). parts is updated in place
+    and holds the force and torque of this step."""
+    g, parts.F, parts.T = links_and_forces(g, owner, mask, parts, rho0)
+    solid = _solid(mask, owner)
+    gnew = collide(post_streaming(g), tau, G, gbody, solid)
+    advance(parts)
+    gnew, owner = remesh(gnew, owner, mask, parts, rho0)
+    return gnew, owner
+
+
+def fluid_momentum(g, owner, mask):
+    """Momentum of the populations held at fluid nodes (post-collision)."""
+    fluid = ~_solid(mask, owner)
+    return np.einsum("kiabc,id->d", g * fluid, VEL.astype(np.float64))
+
+
+def fluid_mass(g, owner, mask):
+    fluid = ~_solid(mask, owner)
+    return float((g * fluid).sum())

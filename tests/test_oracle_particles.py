@@ -1,0 +1,149 @@
+"""Pins of the moving-particle oracle (``oracle.particles``) against what the
+method and the mathematics fix, independently of its own code:
+
+* fixed particles at rest are static solids: the state follows the C oracle's
+  static-mask step (a separate formulation: push streaming with the bounce
+  read-side);
+* the total momentum of fluid and particles is conserved, through the
+  moving-wall bounce (Eq. LADDFLBE), the link forces (Eq. FORCEPP,
+  Eq. FORCEPARTEQ), the leap-frog update (Eq. PARDYN) and re-meshing;
+* a uniform flow at the wall velocity is a fixed point with zero force and
+  torque (the bias 2 rho w_i u_b . c_i / c_s^2 turns f^eq_i(U) into
+  f^eq_opp(i)(U) exactly);
+* a sphere centred on a node, rotating in fluid at rest, feels no force and
+  a torque antiparallel to its rotation (the symmetry of the cubic link set
+  fixes the direction, dissipation the sign);
+* a translating particle that covers no new node conserves the fluid mass
+  exactly (the bias sums to zero over the closed set of links).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import lb_numpy as ln
+from oracle import particles as op
+
+
+def fluid_fields(shape, seed, G):
+    nz, ny, nx = shape
+    rng = np.random.default_rng(seed)
+    rA = 0.5 + 0.05 * rng.uniform(-1, 1, shape)
+    rB = 1.0 - rA
+    u = 0.01 * rng.normal(size=(3,) + shape)
+    return rA, rB, u
+
+
+def test_fixed_particles_at_rest_are_static_solids():
+    shape = (14, 16, 18)          # (nz, ny, nx)
+    nz, ny, nx = shape
+    parts = op.Particles([[4.3, 5.1, 6.6], [12.2, 11.4, 5.0]], radius=2.6, mass=0.0)
+    owner = op.coverage(shape, parts.r, parts.radius)
+    mask = (owner >= 0).astype(np.uint8)
+    rA, rB, u = fluid_fields(shape, 1, 0.9)
+    tau, G, steps = 0.8, 0.9, 6
+    rho0 = (rA[mask == 0].mean(), rB[mask == 0].mean())
+    g = op.init(rA, rB, u, None, owner)
+    for _ in range(steps):
+        g, owner = op.step(g, owner, None, parts, tau, G, rho0)
+    got = ln.to_public(op.pulled(g, owner, None, parts, rho0))
+    want = oracle.run(oracle.init(rA, rB, u, mask), steps, tau, G, None, mask)
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+    assert np.abs(parts.F).max() > 0          # the links were found
+
+
+def test_total_momentum_is_conserved_through_remeshing():
+    shape = (16, 16, 20)
+    rA, rB, u = fluid_fields(shape, 2, 0.6)
+    parts = op.Particles([[5.2, 6.1, 7.3], [14.6, 11.2, 8.4]], v=[[0.3, -0.2, 0.1], [-0.25, 0.1, 0.3]],
+                         w=[[0.0, 0.01, -0.02], [0.02, 0.0, 0.01]], radius=2.4, mass=40.0)
+    owner = op.coverage(shape, parts.r, parts.radius)
+    rho0 = (0.5, 0.5)
+    g = op.init(rA, rB, u, None, owner)
+    owner0 = owner.copy()
+
+    def total(g, owner):
+        return op.fluid_momentum(g, owner, None) + parts.mass * parts.v.sum(axis=0)
+
+    p0 = total(g, owner)
+    scale = np.abs(g).sum() * 1e-2
+    for _ in range(5):
+        g, owner = op.step(g, owner, None, parts, 0.9, 0.6, rho0)
+        assert np.abs(total(g, owner) - p0).max() <= 1e-13 * scale
+    assert (owner != owner0).sum() > 10      # nodes were covered and uncovered
+
+
+def test_uniform_flow_at_the_wall_velocity_is_a_fixed_point():
+    shape = (14, 14, 16)
+    nz, ny, nx = shape
+    U = np.array([0.04, -0.03, 0.02])
+    parts = op.Particles([[7.4, 6.7, 6.9]], v=[U], radius=3.1, mass=0.0)
+    owner = op.coverage(shape, parts.r, parts.radius)
+    rho0 = (0.7, 0.3)
+    fluid = owner < 0
+    uu = np.broadcast_to(U[:, None, None, None], (3,) + shape)
+    g = np.stack([ln.equilibrium(np.full(shape, rho0[k]), uu) for k in range(2)]) * fluid
+    g1, owner1 = op.step(g, owner, None, parts, 0.8, 0.0, rho0)
+    assert np.array_equal(owner1, owner)
+    assert np.abs(g1 - g).max() <= 1e-15
+    assert np.abs(parts.F).max() <= 1e-13 and np.abs(parts.T).max() <= 1e-12
+
+
+@pytest.mark.parametrize("axis", [0, 2])
+def test_rotating_sphere_torque_opposes_rotation(axis):
+    shape = (20, 20, 20)
+    w = np.zeros(3)
+    w[axis] = 2e-3
+    parts = op.Particles([[10.0, 10.0, 10.0]], w=[w], radius=4.2, mass=0.0)
+    owner = op.coverage(shape, parts.r, parts.radius)
+    rho0 = (0.5, 0.5)
+    fluid = owner < 0
+    g = np.stack([ln.equilibrium(np.full(shape, rho0[k]), np.zeros((3,) + shape)) for k in range(2)]) * fluid
+    op.step(g, owner, None, parts, 1.0, 0.0, rho0)
+    T = parts.T[0]
+    assert np.abs(parts.F).max() <= 1e-14
+    assert T[axis] < 0
+    others = [a for a in range(3) if a != axis]
+    assert np.abs(T[others]).max() <= 1e-12 * abs(T[axis])
+
+
+def test_translating_particle_conserves_fluid_mass():
+    shape = (16, 16, 16)
+    rA, rB, u = fluid_fields(shape, 3, 0.8)
+    parts = op.Particles([[8.0, 8.0, 8.0]], v=[[1e-4, -2e-4, 1e-4]], w=[[1e-3, 0.0, -1e-3]], radius=3.5,
+                         mass=500.0)
+    owner = op.coverage(shape, parts.r, parts.radius)
+    g = op.init(rA, rB, u, None, owner)
+    m0 = op.fluid_mass(g, owner, None)
+    owner0 = owner.copy()
+    for _ in range(4):
+        g, owner = op.step(g, owner, None, parts, 0.9, 0.8, (0.5, 0.5))
+    assert np.array_equal(owner, owner0)
+    assert abs(op.fluid_mass(g, owner, None) - m0) <= 1e-13 * m0
+
+
+def test_overlapping_particles_are_rejected():
+    with pytest.raises(ValueError):
+        op.coverage((10, 10, 10), [[3.0, 3.0, 3.0], [5.0, 3.0, 3.0]], 1.5)
+
+
+def test_sphere_carried_by_a_uniform_flow_moves_with_it():
+    """Free flight through re-meshing: a heavy sphere moving with the
+    surrounding uniform flow feels no force, so it advances U per step
+    (leap-frog), and the nodes it uncovers are refilled with the same
+    uniform equilibrium."""
+    shape = (12, 12, 16)
+    U = np.array([0.3, -0.1, 0.05])
+    parts = op.Particles([[6.3, 5.8, 6.1]], v=[U], radius=2.7, mass=1e12)
+    owner = op.coverage(shape, parts.r, parts.radius)
+    owner0 = owner.copy()
+    rho0 = (0.6, 0.4)
+    uu = np.broadcast_to(U[:, None, None, None], (3,) + shape)
+    feq = np.stack([ln.equilibrium(np.full(shape, rho0[k]), uu) for k in range(2)])
+    g = feq * (owner < 0)
+    r0 = parts.r[0].copy()
+    steps = 6
+    for _ in range(steps):
+        g, owner = op.step(g, owner, None, parts, 0.8, 0.0, rho0)
+    assert (owner != owner0).sum() > 10
+    assert np.abs(parts.r[0] - np.mod(r0 + steps * U, (16, 12, 12))).max() <= 1e-9
+    assert np.abs((g - feq) * (owner < 0)).max() <= 1e-10
