@@ -98,6 +98,8 @@ typedef struct {
                               1/nu_bar = (rho^A/rho)/nu_A + (rho^B/rho)/nu_B) */
     double cg_sigma;       /* colour gradient: surface tension, >= 0 (A = 9 omega sigma / 4) */
     double cg_beta;        /* colour gradient: recolouring parameter, in [0, 1] */
+    int max_particles;     /* > 0: room for that many moving spheres (lb_particles_set);
+                              needs the Shan-Chen model, LB_KERNEL_FUSED, no recording */
 } lb_options;
 
 /* Fill *opt with the defaults above. */
@@ -182,6 +184,37 @@ lb_status lb_backward(lb_ctx* ctx, const float* d_dL_drhoA, const float* d_dL_dr
  * launches per lb_step(1), and the tile/grid shape chosen at lb_create. */
 lb_status lb_launch_info(const lb_ctx* ctx, int* launches_per_step, int* grid_blocks,
                          int* block_threads, int* z_split);
+
+/* Moving rigid spheres (Sec. 2; the particles of Eq. PARDYN), all with one
+ * radius and mass. A node is covered by a sphere when its periodic distance
+ * to the centre is at most the radius; covered nodes hold no fluid. Each
+ * lb_step then runs, per step: the moving-wall halfway bounce-back at every
+ * link from a fluid node x to a covered node x + c_i (Eq. LADDFLBE with the
+ * wall velocity u_b = v + w x (r_b - r) at the link midpoint r_b, Eq. UPI,
+ * and rho = rho0^k of lb_init), whose exchanged momentum sums in FP64 into
+ * the sphere's force and torque (Eq. FORCEPP, FORCEPARTEQ, TORQUEPARTEQ);
+ * the fluid step; the leap-frog update v += F/m, r += v, w += T/I with
+ * I = 2 m R^2 / 5 (Eq. PARDYN); and re-meshing: nodes a sphere leaves become
+ * fluid at rho0^k and the local wall velocity, nodes it reaches give their
+ * fluid's momentum to it (total momentum is conserved).
+ *   n            number of spheres, 0 <= n <= opt->max_particles.
+ *   r, v, w      HOST arrays of 3n doubles (x, y, z per sphere): centres
+ *                (any real coordinates, wrapped into the box), velocities
+ *                and angular velocities (NULL = 0).
+ *   radius       > 0; 2 (ceil(radius) + 3) + 1 <= min(nx, ny, nz).
+ *   mass         > 0, or <= 0 for spheres held fixed (forces still computed).
+ * Call after lb_create and before lb_init (LB_ESTATE otherwise). LB_EINVAL
+ * for bad values, spheres closer than 2 radius (periodic) or covering a
+ * solid node of the mask. Synchronous. */
+lb_status lb_particles_set(lb_ctx* ctx, int n, const double* r, const double* v, const double* w, double radius,
+                           double mass);
+
+/* The spheres after the last step, into HOST arrays of 3n doubles (any may
+ * be NULL): r, v, w as above, and F, T = the force and torque of the last
+ * step's links. LB_ESTATE (arrays still filled) when a step met spheres that
+ * touch each other or the mask, or a sphere faster than one node per step:
+ * the run is no longer valid. Synchronous. */
+lb_status lb_particles_get(lb_ctx* ctx, double* r, double* v, double* w, double* F, double* T);
 
 /* Bounce-back links of the mask (pairs of a fluid node x and a direction i
  * with x + c_i solid, Eq. LADDFLBE), as lb_create arranged them: *listed =

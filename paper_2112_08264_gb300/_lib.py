@@ -28,6 +28,7 @@ class LbOptions(ctypes.Structure):
         ("cg_nu_B", ctypes.c_double),
         ("cg_sigma", ctypes.c_double),
         ("cg_beta", ctypes.c_double),
+        ("max_particles", ctypes.c_int),
     ]
 
 
@@ -75,6 +76,9 @@ def lib():
     L.lb_steps_done.restype = ctypes.c_longlong
     L.lb_backward.argtypes = [_VP, _FP, _FP, _FP, _FP, ctypes.POINTER(ctypes.c_double)]
     L.lb_launch_info.argtypes = [_VP] + [ctypes.POINTER(ctypes.c_int)] * 4
+    _DP = ctypes.POINTER(ctypes.c_double)
+    L.lb_particles_set.argtypes = [_VP, ctypes.c_int, _DP, _DP, _DP, ctypes.c_double, ctypes.c_double]
+    L.lb_particles_get.argtypes = [_VP, _DP, _DP, _DP, _DP, _DP]
     L.lb_link_info.argtypes = [_VP, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                                ctypes.POINTER(ctypes.c_int)]
     L.lb_moments_noalloc.argtypes = ([ctypes.c_int] * 3 + [ctypes.c_float, ctypes.POINTER(ctypes.c_double),
@@ -87,7 +91,8 @@ def lib():
     L.lb_last_error.argtypes = []
     L.lb_last_error.restype = ctypes.c_char_p
     for name in ("lb_create", "lb_set_stream", "lb_init", "lb_step", "lb_moments", "lb_stats",
-                 "lb_get_state", "lb_set_state", "lb_backward", "lb_launch_info", "lb_link_info"):
+                 "lb_get_state", "lb_set_state", "lb_backward", "lb_launch_info", "lb_link_info",
+                 "lb_particles_set", "lb_particles_get"):
         getattr(L, name).restype = ctypes.c_int
     # one-component BGK (include/lb1.h)
     L.lb1_workspace_bytes.argtypes = [ctypes.c_int] * 4
@@ -116,7 +121,7 @@ def check(status, what):
 
 
 def options(prec="fp32", kernel="fused", rho0=(0.0, 0.0), body_force=(0.0, 0.0, 0.0),
-            ckpt_every=0, ckpt_steps_max=0, model="shan_chen", cg=None):
+            ckpt_every=0, ckpt_steps_max=0, model="shan_chen", cg=None, max_particles=0):
     """lb_options; ``cg`` = dict(nu=(nu_A, nu_B), sigma=, beta=) for the
     colour-gradient model."""
     o = LbOptions()
@@ -133,6 +138,7 @@ def options(prec="fp32", kernel="fused", rho0=(0.0, 0.0), body_force=(0.0, 0.0, 
         o.body_force[a] = float(body_force[a])
     o.ckpt_every = int(ckpt_every)
     o.ckpt_steps_max = int(ckpt_steps_max)
+    o.max_particles = int(max_particles)
     return o
 
 

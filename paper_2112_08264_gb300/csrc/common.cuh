@@ -56,6 +56,7 @@ struct Phys {
     float cg_inu[2]; // colour gradient: 1 / nu of the pure components
     float cg_sigma;  // colour gradient: surface tension
     float cg_beta;   // colour gradient: recolouring parameter
+    int slots;       // state readers: 1 = every solid slot a fluid node pulls is written (pull it as is)
 };
 
 // solid-site flags: bit 0 = this node is solid; bit i (1..18) = node x - c_i
@@ -379,7 +380,7 @@ __device__ __forceinline__ float2 density_at(const S* __restrict__ src, const ui
         if (fl & kSolid) return make_float2(-p.rho0[0], -p.rho0[1]);
     }
     float d[2][Q];
-    pull<S, MASK>(src, g, P, fl, d);
+    pull<S, MASK>(src, g, P, p.slots ? 0u : fl, d);
     return make_float2(dens_sum(d[0]), dens_sum(d[1]));
 }
 

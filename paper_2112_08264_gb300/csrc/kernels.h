@@ -97,7 +97,32 @@ bool tiles_in_kernel(const StepLaunch& L);
 cudaError_t launch_reflect(int prec, void* g_state, const uint32_t* flags, const LinkList& links, bool with_tiles,
                            const Geom& g, cudaStream_t st);
 
-// Internal state from a post-streaming population field: either the
+// Moving spheres (lb_particles.cu). Arrays of 3n doubles on the device;
+// owner[s] = p + 1 when sphere p covers site s, 0 otherwise; err collects
+// bit 1 (spheres touching each other or the mask) and bit 2 (a sphere faster
+// than one node per step).
+struct Spheres {
+    double *r = nullptr, *v = nullptr, *w = nullptr, *F = nullptr, *T = nullptr;
+    int* owner = nullptr;
+    int* err = nullptr;
+    int n = 0;
+    double radius = 0.0, mass = 0.0, inertia = 0.0;
+    int half = 0;   // box half-width around a centre: ceil(radius) + 2
+};
+// Moving-wall bounce-back into the solid slots of `state` and, when
+// `forces`, the spheres' force and torque of those links.
+cudaError_t launch_sphere_links(int prec, void* state, const uint32_t* flags, const Spheres& S, bool forces,
+                                const Geom& g, const Phys& p, cudaStream_t st);
+// Leap-frog update, then re-meshing of `state` and the flags around every
+// sphere (static solids from `mask`, may be nullptr).
+cudaError_t launch_sphere_move(int prec, void* state, uint32_t* flags, const uint8_t* mask, const Spheres& S,
+                               const Geom& g, const Phys& p, cudaStream_t st);
+// Coverage of freshly placed spheres (owner zeroed first) and the flags of
+// the whole grid from `mask` and the coverage.
+cudaError_t launch_sphere_place(uint32_t* flags, const uint8_t* mask, const Spheres& S, const Geom& g,
+                                cudaStream_t st);
+
+// Internal state from a post-streaming population field:// Internal state from a post-streaming population field: either the
 // equilibrium of (rhoA, rhoB, u) (f == nullptr) or the given f (float,
 // [k][i][s]). Inverse of the pull: g_j(y) = f_j(y + c_j) if y + c_j is fluid,
 // else f_opp(j)(y); solid slots are filled as launch_reflect fills them.

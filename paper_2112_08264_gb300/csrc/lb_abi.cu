@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -40,7 +41,7 @@ namespace {
 size_t store_bytes(int prec) { return prec == LB_FP32 ? 4 : 2; }
 
 struct Layout {
-    size_t pop[2], mask, flags, links, tent, tstart, cursor, rho, red_part, red_out;
+    size_t pop[2], mask, flags, links, tent, tstart, cursor, rho, red_part, red_out, owner, spheres;
     size_t ckpt, ckpt_slots, seg, adj;
     size_t state_bytes;
     size_t total;
@@ -59,6 +60,10 @@ bool valid_options(const lb_options& o) {
     for (double g : o.body_force)
         if (!std::isfinite(g)) return false;
     if (o.ckpt_every < 0 || o.ckpt_steps_max < 0) return false;
+    if (o.max_particles < 0) return false;
+    if (o.max_particles > 0 &&
+        (o.model != LB_MODEL_SHAN_CHEN || o.kernel != LB_KERNEL_FUSED || o.ckpt_every != 0))
+        return false;
     if (o.ckpt_every > 0 && o.ckpt_steps_max < 1) return false;
     if (o.model != LB_MODEL_SHAN_CHEN && o.model != LB_MODEL_COLOUR_GRADIENT) return false;
     if (o.model == LB_MODEL_COLOUR_GRADIENT) {
@@ -90,6 +95,11 @@ Layout make_layout(int nx, int ny, int nz, const lb_options& o) {
     L.rho = off; off += align256(2 * N * 4);
     L.red_part = off; off += align256((size_t)kRedBlocks * kRedVals * 8);
     L.red_out = off; off += align256(kRedVals * 8);
+    if (o.max_particles > 0) {
+        L.owner = off; off += align256(N * 4);   // sphere covering each site
+        // r, v, w, F, T (3 doubles each per sphere) and the error word
+        L.spheres = off; off += align256((size_t)o.max_particles * 15 * 8 + 8);
+    }
     if (o.ckpt_every > 0) {
         L.ckpt_slots = (size_t)(o.ckpt_steps_max / o.ckpt_every) + 1;
         L.ckpt = off; off += L.ckpt_slots * L.state_bytes;
@@ -124,6 +134,8 @@ struct lb_ctx {
     AsyncPlan plan;
     AsyncPlan adjplan;
     LinkList links;     // write-side bounce-back links of the mask
+    bool particles;     // room for moving spheres (max_particles > 0)
+    Spheres sph;        // the spheres (device arrays in the workspace)
     // recording for the adjoint
     bool recording;       // lb_init was called with ckpt_every > 0 and the run is intact
     double rho0_d[2];
@@ -154,11 +166,26 @@ lb_status cuda_status(const char* what, cudaError_t e) {
     return LB_ECUDA;
 }
 
+// solid flags, when any node can be solid (a mask or spheres)
+const uint32_t* flags_of(const lb_ctx* c) { return c->has_mask || c->particles ? c->flags : nullptr; }
+
+// With spheres, the state readers first write the spheres' slots (no
+// forces) and then pull every slot as stored.
+cudaError_t reader_phys(lb_ctx* c, Phys& p) {
+    p = c->p;
+    if (!c->particles) return cudaSuccess;
+    p.slots = 1;
+    return launch_sphere_links(c->opt.prec, c->pop[c->cur], c->flags, c->sph, false, c->g, c->p, c->stream);
+}
+
 lb_status run_reduction(lb_ctx* c, double out[kRedVals], bool stats, const float* rA = nullptr,
                         const float* rB = nullptr, const float* u = nullptr) {
-    cudaError_t e = stats ? launch_stats(c->opt.prec, c->pop[c->cur], c->has_mask ? c->flags : nullptr,
-                                         c->red_part, c->red_out, c->g, c->p, c->stream)
-                          : launch_check_init(rA, rB, u, c->has_mask ? c->flags : nullptr, c->red_part,
+    Phys rp;
+    cudaError_t e = stats ? reader_phys(c, rp) : cudaSuccess;
+    if (e == cudaSuccess)
+        e = stats ? launch_stats(c->opt.prec, c->pop[c->cur], flags_of(c), c->red_part, c->red_out, c->g, rp,
+                                 c->stream)
+                  : launch_check_init(rA, rB, u, flags_of(c), c->red_part,
                                               c->red_out, c->g, c->opt.model == LB_MODEL_COLOUR_GRADIENT,
                                               c->stream);
     if (e != cudaSuccess) return cuda_status("reduction launch", e);
@@ -229,10 +256,14 @@ lb_status lb_create(int nx, int ny, int nz, float tau, float G, const uint8_t* m
     c->red_part = reinterpret_cast<double*>(c->ws + L.red_part);
     c->red_out = reinterpret_cast<double*>(c->ws + L.red_out);
     c->has_mask = mask != nullptr;
+    c->particles = o.max_particles > 0;
     c->sm_count = sms;
     fused_geometry(nx, ny, nz, sms, &c->tiles, &c->zsplit, &c->threads);
-    c->plan = plan_fused_async(nx, ny, nz, sms, o.prec, mask != nullptr, (size_t)smem_optin);
-    if (o.kernel == LB_KERNEL_FUSED && c->plan.nst < 2) {   // no tile fits in shared memory
+    // spheres make solid nodes too: the masked kernel (flag boxes in shared memory) steps them
+    c->plan = plan_fused_async(nx, ny, nz, sms, o.prec, mask != nullptr || o.max_particles > 0,
+                               (size_t)smem_optin);
+    if ((o.kernel == LB_KERNEL_FUSED && c->plan.nst < 2) || (c->particles && !c->plan.box)) {
+        // no tile fits in shared memory, or spheres on a grid the box kernel cannot step
         delete c;
         return LB_EINVAL;
     }
@@ -262,6 +293,27 @@ lb_status lb_create(int nx, int ny, int nz, float tau, float G, const uint8_t* m
             return cuda_status("mask upload", e);
         }
     }
+    if (c->particles) {
+        Spheres& S = c->sph;
+        double* a = reinterpret_cast<double*>(c->ws + L.spheres);
+        const size_t P3 = (size_t)o.max_particles * 3;
+        S.r = a;
+        S.v = a + P3;
+        S.w = a + 2 * P3;
+        S.F = a + 3 * P3;
+        S.T = a + 4 * P3;
+        S.err = reinterpret_cast<int*>(a + 5 * P3);
+        S.owner = reinterpret_cast<int*>(c->ws + L.owner);
+        S.n = 0;
+        if (!mask) c->links.sites = reinterpret_cast<const uint32_t*>(c->ws + L.links);   // no static links
+        e = cudaMemsetAsync(S.err, 0, sizeof(int), c->stream);
+        if (e == cudaSuccess) e = launch_sphere_place(c->flags, mask ? c->mask_dev : nullptr, S, c->g, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            delete c;
+            return cuda_status("sphere setup", e);
+        }
+    }
     *out = c;
     return LB_OK;
 }
@@ -284,7 +336,7 @@ lb_status lb_init(lb_ctx* c, const float* rA, const float* rB, const float* u) {
     c->p.rho0[0] = (float)c->rho0_d[0];
     c->p.rho0[1] = (float)c->rho0_d[1];
     c->cur = 0;
-    cudaError_t e = launch_unstream(c->opt.prec, c->pop[0], c->has_mask ? c->flags : nullptr, nullptr, rA, rB,
+    cudaError_t e = launch_unstream(c->opt.prec, c->pop[0], flags_of(c), nullptr, rA, rB,
                                     u, c->g, c->p, c->stream);
     if (e == cudaSuccess && c->opt.ckpt_every > 0)
         e = cudaMemcpyAsync(c->ws + c->L.ckpt, c->pop[0], c->L.state_bytes, cudaMemcpyDeviceToDevice, c->stream);
@@ -301,7 +353,7 @@ StepLaunch step_launch(const lb_ctx* c) {
     StepLaunch S;
     S.prec = c->opt.prec;
     S.kernel = c->opt.kernel;
-    S.flags = c->has_mask ? c->flags : nullptr;
+    S.flags = flags_of(c);
     S.rho = c->rho;
     S.mom_out = nullptr;
     S.g = c->g;
@@ -333,7 +385,13 @@ lb_status lb_step(lb_ctx* c, int n) {
     for (int t = 0; t < n; ++t) {
         S.src = c->pop[c->cur];
         S.dst = c->pop[1 - c->cur];
-        cudaError_t e = launch_step(S, c->stream);
+        cudaError_t e = cudaSuccess;
+        if (c->particles)   // the spheres' links: slots of src, forces and torques
+            e = launch_sphere_links(c->opt.prec, c->pop[c->cur], c->flags, c->sph, true, c->g, c->p, c->stream);
+        if (e == cudaSuccess) e = launch_step(S, c->stream);
+        if (e == cudaSuccess && c->particles)   // leap-frog and re-meshing of dst
+            e = launch_sphere_move(c->opt.prec, c->pop[1 - c->cur], c->flags, c->has_mask ? c->mask_dev : nullptr,
+                                   c->sph, c->g, c->p, c->stream);
         if (e != cudaSuccess) return cuda_status("step", e);
         c->cur ^= 1;
         c->steps += 1;
@@ -350,11 +408,12 @@ lb_status lb_step(lb_ctx* c, int n) {
 lb_status lb_moments(lb_ctx* c, float* rA, float* rB, float* u) {
     if (!c) return LB_EINVAL;
     if (!c->initialized) return LB_ESTATE;
-    const uint32_t* fl = c->has_mask ? c->flags : nullptr;
-    cudaError_t e = cudaSuccess;
-    if (u) e = launch_densities(c->opt.prec, c->pop[c->cur], fl, c->rho, c->g, c->p, c->stream);
+    const uint32_t* fl = flags_of(c);
+    Phys rp;
+    cudaError_t e = reader_phys(c, rp);
+    if (e == cudaSuccess && u) e = launch_densities(c->opt.prec, c->pop[c->cur], fl, c->rho, c->g, rp, c->stream);
     if (e == cudaSuccess)
-        e = launch_moments(c->opt.prec, c->pop[c->cur], fl, c->rho, rA, rB, u, c->g, c->p, c->stream);
+        e = launch_moments(c->opt.prec, c->pop[c->cur], fl, c->rho, rA, rB, u, c->g, rp, c->stream);
     return cuda_status("moments", e);
 }
 
@@ -371,15 +430,17 @@ lb_status lb_stats(lb_ctx* c, double out5[5]) {
 lb_status lb_get_state(lb_ctx* c, float* dst) {
     if (!c || !dst) return LB_EINVAL;
     if (!c->initialized) return LB_ESTATE;
-    return cuda_status("get_state", launch_get_state(c->opt.prec, c->pop[c->cur], c->has_mask ? c->flags : nullptr,
-                                                     dst, c->g, c->p, c->stream));
+    Phys rp;
+    cudaError_t e = reader_phys(c, rp);
+    if (e == cudaSuccess) e = launch_get_state(c->opt.prec, c->pop[c->cur], flags_of(c), dst, c->g, rp, c->stream);
+    return cuda_status("get_state", e);
 }
 
 lb_status lb_set_state(lb_ctx* c, const float* src) {
     if (!c || !src) return LB_EINVAL;
     if (!c->initialized) return LB_ESTATE;
     c->recording = false;   // the recorded trajectory no longer leads to this state
-    return cuda_status("set_state", launch_unstream(c->opt.prec, c->pop[c->cur], c->has_mask ? c->flags : nullptr,
+    return cuda_status("set_state", launch_unstream(c->opt.prec, c->pop[c->cur], flags_of(c),
                                                     src, nullptr, nullptr, nullptr, c->g, c->p, c->stream));
 }
 
@@ -419,13 +480,94 @@ lb_status lb_launch_info(const lb_ctx* c, int* launches, int* blocks, int* threa
     if (!c) return LB_EINVAL;
     const int k = c->opt.kernel;
     // a masked step adds the write-side bounce-back passes (launch_reflect)
-    if (launches) *launches = (k == LB_KERNEL_TWO_PASS ? 2 : 1) + reflect_launches(c);
+    // spheres: their links, and when they move the update, two re-meshing passes and the flags
+    const int sph = !c->particles || c->sph.n == 0 ? 0 : (c->sph.mass > 0.0 ? 5 : 1);
+    if (launches) *launches = (k == LB_KERNEL_TWO_PASS ? 2 : 1) + reflect_launches(c) + sph;
     if (blocks)
         *blocks = k == LB_KERNEL_FUSED ? c->plan.ncols * c->plan.R * c->plan.zsplit
                 : k == LB_KERNEL_FUSED_REG ? c->tiles * c->zsplit : (int)((c->g.N + 255) / 256);
     if (threads) *threads = k == LB_KERNEL_FUSED ? c->plan.threads : k == LB_KERNEL_FUSED_REG ? c->threads : 256;
     if (zsplit) *zsplit = k == LB_KERNEL_FUSED ? c->plan.zsplit : c->zsplit;
     return LB_OK;
+}
+
+lb_status lb_particles_set(lb_ctx* c, int n, const double* r, const double* v, const double* w, double radius,
+                           double mass) {
+    if (!c) return LB_EINVAL;
+    if (!c->particles || n < 0 || n > c->opt.max_particles || (n > 0 && !r)) return LB_EINVAL;
+    if (c->initialized) return LB_ESTATE;
+    if (!std::isfinite(radius) || !(radius > 0.0) || !std::isfinite(mass)) return LB_EINVAL;
+    const int half = (int)std::ceil(radius) + 2;
+    if (2 * (half + 1) + 1 > std::min(c->g.nx, std::min(c->g.ny, c->g.nz))) return LB_EINVAL;
+    const int dims[3] = {c->g.nx, c->g.ny, c->g.nz};
+    std::vector<double> h(15 * (size_t)n, 0.0);   // r, v, w, F, T
+    for (int q = 0; q < n; ++q)
+        for (int a = 0; a < 3; ++a) {
+            const double x = r[3 * q + a];
+            const double vv = v ? v[3 * q + a] : 0.0, ww = w ? w[3 * q + a] : 0.0;
+            if (!std::isfinite(x) || !std::isfinite(vv) || !std::isfinite(ww)) return LB_EINVAL;
+            const double m = std::fmod(x, (double)dims[a]);
+            h[3 * q + a] = m < 0.0 ? m + dims[a] : m;
+            h[3 * (size_t)n + 3 * q + a] = vv;
+            h[6 * (size_t)n + 3 * q + a] = ww;
+        }
+    // spheres closer than two radii (periodic) would share nodes
+    for (int p = 0; p < n; ++p)
+        for (int q = p + 1; q < n; ++q) {
+            double d2 = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                double d = h[3 * p + a] - h[3 * q + a];
+                d -= dims[a] * std::nearbyint(d / dims[a]);
+                d2 += d * d;
+            }
+            if (d2 <= 4.0 * radius * radius) return LB_EINVAL;
+        }
+    Spheres& S = c->sph;
+    const size_t P3 = (size_t)c->opt.max_particles * 3;
+    cudaError_t e = cudaSuccess;
+    if (n > 0) {
+        const double* src[5] = {h.data(), h.data() + 3 * (size_t)n, h.data() + 6 * (size_t)n,
+                                h.data() + 9 * (size_t)n, h.data() + 12 * (size_t)n};
+        double* dst[5] = {S.r, S.v, S.w, S.F, S.T};
+        for (int k = 0; k < 5 && e == cudaSuccess; ++k)
+            e = cudaMemcpyAsync(dst[k], src[k], 3 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    }
+    (void)P3;
+    S.n = n;
+    S.radius = radius;
+    S.mass = mass;
+    S.inertia = 0.4 * mass * (radius * radius);
+    S.half = half;
+    int err = 0;
+    if (e == cudaSuccess) e = cudaMemsetAsync(S.err, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = launch_sphere_place(c->flags, c->has_mask ? c->mask_dev : nullptr, S, c->g, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, S.err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_status("particles_set", e);
+    if (err) {   // a sphere covers a solid node of the mask: no spheres
+        S.n = 0;
+        e = launch_sphere_place(c->flags, c->has_mask ? c->mask_dev : nullptr, S, c->g, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        return e == cudaSuccess ? LB_EINVAL : cuda_status("particles_set", e);
+    }
+    return LB_OK;
+}
+
+lb_status lb_particles_get(lb_ctx* c, double* r, double* v, double* w, double* F, double* T) {
+    if (!c) return LB_EINVAL;
+    if (!c->particles) return LB_ESTATE;
+    const Spheres& S = c->sph;
+    const size_t bytes = 3 * (size_t)S.n * sizeof(double);
+    double* out[5] = {r, v, w, F, T};
+    const double* src[5] = {S.r, S.v, S.w, S.F, S.T};
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 5 && e == cudaSuccess; ++k)
+        if (out[k] && bytes) e = cudaMemcpyAsync(out[k], src[k], bytes, cudaMemcpyDeviceToHost, c->stream);
+    int err = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, S.err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_status("particles_get", e);
+    return err ? LB_ESTATE : LB_OK;
 }
 
 lb_status lb_link_info(const lb_ctx* c, long long* listed, long long* in_tile, int* in_kernel) {

@@ -296,7 +296,7 @@ __global__ void get_state_kernel(const S* __restrict__ src, const uint32_t* __re
     PullIdx P;
     pull_indices(g, x, y, z, P);
     float d[2][Q];
-    pull<S, MASK>(src, g, P, fl, d);
+    pull<S, MASK>(src, g, P, p.slots ? 0u : fl, d);
     static_for<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
 #pragma unroll
@@ -336,7 +336,7 @@ __global__ void moments_kernel(const S* __restrict__ src, const uint32_t* __rest
     PullIdx P;
     pull_indices(g, x, y, z, P);
     float d[2][Q];
-    pull<S, MASK>(src, g, P, fl, d);
+    pull<S, MASK>(src, g, P, p.slots ? 0u : fl, d);
     float dA, dB, j[3];
     sums(d, dA, dB, j);
     const float rA = p.rho0[0] + dA, rB = p.rho0[1] + dB;
@@ -386,7 +386,7 @@ stats_kernel(const S* __restrict__ src, const uint32_t* __restrict__ flags, doub
         PullIdx P;
         pull_indices(g, x, y, z, P);
         float d[2][Q];
-        pull<S, MASK>(src, g, P, fl, d);
+        pull<S, MASK>(src, g, P, p.slots ? 0u : fl, d);
         // per-node sums in FP32 (19 terms), accumulated across nodes in FP64
         float dA, dB, j[3];
         sums(d, dA, dB, j);

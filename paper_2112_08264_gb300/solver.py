@@ -42,7 +42,7 @@ class Solver:
 
     def __init__(self, nx, ny, nz, tau, G, mask=None, prec="fp32", kernel="fused", rho0=(0.0, 0.0),
                  body_force=(0.0, 0.0, 0.0), ckpt_every=0, ckpt_steps_max=0, device=None, stream=None,
-                 model="shan_chen", cg=None):
+                 model="shan_chen", cg=None, max_particles=0):
         L = _lib.lib()
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.shape = (self.nz, self.ny, self.nx)
@@ -50,7 +50,9 @@ class Solver:
         self.tau, self.G = float(tau), float(G)
         self.prec, self.kernel = prec, kernel
         self.model = model
-        self.opt = _lib.options(prec, kernel, rho0, body_force, ckpt_every, ckpt_steps_max, model, cg)
+        self.opt = _lib.options(prec, kernel, rho0, body_force, ckpt_every, ckpt_steps_max, model, cg,
+                                max_particles)
+        self.n_particles = 0
         nbytes = _lib.workspace_bytes(self.nx, self.ny, self.nz, self.opt)
         if nbytes == 0:
             raise ValueError("invalid grid or options")
@@ -147,6 +149,29 @@ class Solver:
         _lib.check(_lib.lib().lb_launch_info(self._h, *[ctypes.byref(x) for x in v]), "lb_launch_info")
         return {"launches_per_step": v[0].value, "grid_blocks": v[1].value,
                 "block_threads": v[2].value, "z_split": v[3].value}
+
+    def set_particles(self, r, v=None, w=None, radius=5.0, mass=1.0):
+        """Place moving rigid spheres (``lb_particles_set``): centres ``r``,
+        velocities ``v`` and angular velocities ``w`` as (n, 3) arrays, one
+        radius and mass (mass <= 0: held fixed). Before ``init``."""
+        r = np.ascontiguousarray(np.asarray(r, np.float64).reshape(-1, 3))
+        n = len(r)
+        arr = lambda a: None if a is None else np.ascontiguousarray(np.asarray(a, np.float64).reshape(n, 3))
+        v, w = arr(v), arr(w)
+        ptr = lambda a: None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        _lib.check(_lib.lib().lb_particles_set(self._h, n, ptr(r), ptr(v), ptr(w), float(radius), float(mass)),
+                   "lb_particles_set")
+        self.n_particles = n
+
+    def particles(self):
+        """The spheres after the last step: dict of (n, 3) arrays r, v, w and
+        the last step's force F and torque T (``lb_particles_get``)."""
+        n = self.n_particles
+        out = {k: np.zeros((n, 3)) for k in ("r", "v", "w", "F", "T")}
+        ptr = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        _lib.check(_lib.lib().lb_particles_get(self._h, *[ptr(out[k]) for k in ("r", "v", "w", "F", "T")]),
+                   "lb_particles_get")
+        return out
 
     def link_info(self):
         """Bounce-back links of the mask: ``listed`` in the per-velocity pass

@@ -1,0 +1,189 @@
+"""Moving rigid spheres on the GPU (``lb_particles_set`` / ``lb_step``)
+against the FP64 particle oracle (``oracle.particles``), through the C ABI.
+
+Bars: fixed spheres at rest give, bit for bit, the state of the static mask
+they cover (their slots carry no bias); moving spheres follow the oracle
+step by step -- pulled states within a few FP32 ulps of the largest
+population, positions, velocities, forces and torques within 1e-5 of their
+scale -- through re-meshing; the total momentum of fluid and spheres is
+conserved; the benchmark's 256^3 launch configuration reproduces a tiled
+32^3 oracle run at every site and every sphere."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import lb_numpy as ln  # noqa: E402
+from oracle import particles as op  # noqa: E402
+from paper_2112_08264_gb300 import Solver, build, inputs  # noqa: E402
+from paper_2112_08264_gb300 import _lib  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+
+
+def dev(a):
+    return torch.tensor(np.asarray(a, dtype=np.float32), device="cuda")
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def fields(shape, seed):
+    nx, ny, nz = shape
+    rng = np.random.default_rng(seed)
+    rA = 0.5 + 0.05 * rng.uniform(-1, 1, (nz, ny, nx))
+    u = 0.01 * rng.normal(size=(3, nz, ny, nx))
+    return f32(rA), f32(1.0 - rA), f32(u)
+
+
+def gpu_run(shape, spheres, steps, tau, G, rA, rB, u, prec="fp32", mask=None):
+    nx, ny, nz = shape
+    s = Solver(nx, ny, nz, tau, G, mask=mask, prec=prec, max_particles=max(1, len(spheres["r"])))
+    s.set_particles(spheres["r"], spheres.get("v"), spheres.get("w"), spheres["radius"], spheres["mass"])
+    s.init(dev(rA), dev(rB), dev(u))
+    return s
+
+
+def oracle_init(shape, spheres, rA, rB, u, mask=None):
+    nx, ny, nz = shape
+    parts = op.Particles(spheres["r"], spheres.get("v"), spheres.get("w"), spheres["radius"], spheres["mass"])
+    owner = op.coverage((nz, ny, nx), parts.r, parts.radius)
+    fluid = (owner < 0) if mask is None else (owner < 0) & (mask == 0)
+    rho0 = (rA[fluid].mean(), rB[fluid].mean())
+    g = op.init(rA, rB, u, mask, owner)
+    return g, owner, parts, rho0
+
+
+TWO = dict(r=[[9.3, 8.4, 7.7], [23.6, 17.2, 12.9]], v=[[0.21, -0.12, 0.07], [-0.15, 0.08, 0.18]],
+           w=[[0.0, 0.01, -0.02], [0.015, 0.0, 0.01]], radius=3.2, mass=60.0)
+
+
+def test_fixed_spheres_at_rest_equal_the_static_mask_bitwise():
+    shape = (32, 24, 20)
+    nx, ny, nz = shape
+    sph = dict(r=[[9.3, 8.4, 7.7], [23.6, 17.2, 12.9]], radius=3.2, mass=0.0)
+    rA, rB, u = fields(shape, 1)
+    s = gpu_run(shape, sph, 0, 0.9, 0.8, rA, rB, u)
+    mask = (op.coverage((nz, ny, nx), np.array(sph["r"]), sph["radius"]) >= 0).astype(np.uint8)
+    m = Solver(nx, ny, nz, 0.9, 0.8, mask=mask)
+    m.init(dev(rA), dev(rB), dev(u))
+    for _ in range(3):
+        s.step(4)
+        m.step(4)
+        assert torch.equal(s.get_state(), m.get_state())
+    p = s.particles()
+    assert np.array_equal(p["r"], np.array(sph["r"])) and np.abs(p["F"]).max() > 0
+
+
+# per-quantity bars: FP32 storage; FP16 storage (forces sum hundreds of
+# rounded populations with cancellation, so only positions and velocities
+# are held close)
+BARS = {"fp32": dict(r=1e-5, v=4e-6, w=4e-6, F=4e-6, T=4e-6, state=8e-7),
+        "fp16": dict(r=1e-4, v=5e-2, w=None, F=None, T=None, state=2e-3)}
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_moving_spheres_follow_the_oracle(prec):
+    bars = BARS[prec]
+    shape = (32, 24, 20)
+    nx, ny, nz = shape
+    tau, G, steps = 0.9, 0.6, 8
+    rA, rB, u = fields(shape, 2)
+    s = gpu_run(shape, TWO, 0, tau, G, rA, rB, u, prec=prec)
+    g, owner, parts, rho0 = oracle_init(shape, TWO, rA, rB, u)
+    owner0 = owner.copy()
+    for t in range(steps):
+        s.step(1)
+        g, owner = op.step(g, owner, None, parts, tau, G, rho0)
+        p = s.particles()
+        for k, ref in (("r", parts.r), ("v", parts.v), ("w", parts.w), ("F", parts.F), ("T", parts.T)):
+            if bars[k] is None:
+                continue
+            bar = bars[k] if k == "r" else bars[k] * max(np.abs(ref).max(), 1e-30)
+            assert np.abs(p[k] - ref).max() <= bar, (t, k, p[k], ref)
+    assert (owner != owner0).sum() > 20            # re-meshing happened
+    got = s.get_state().cpu().numpy().astype(np.float64)
+    want = ln.to_public(op.pulled(g, owner, None, parts, rho0))
+    assert np.abs(got - want).max() <= bars["state"] * np.abs(want).max()
+
+
+def test_total_momentum_is_conserved():
+    """stats() reads the pulled state, in which the next step's bounce has
+    already taken the next step's force F from the fluid: fluid momentum +
+    F + sum m v is the conserved total."""
+    shape = (32, 24, 20)
+    rA, rB, u = fields(shape, 3)
+    s = gpu_run(shape, TWO, 0, 0.9, 0.6, rA, rB, u)
+    totals = []
+    for _ in range(8):
+        st = np.array(s.stats())
+        v = s.particles()["v"]
+        s.step(1)
+        F = s.particles()["F"]
+        totals.append(st[2:5] + F.sum(axis=0) + TWO["mass"] * v.sum(axis=0))
+        M = st[0] + st[1]
+    totals = np.array(totals)
+    assert np.abs(totals - totals[0]).max() <= 1e-6 * M
+
+
+def test_rejections():
+    shape = (32, 24, 20)
+    nx, ny, nz = shape
+    rA, rB, u = fields(shape, 4)
+    s = Solver(nx, ny, nz, 1.0, 0.5, max_particles=2)
+    with pytest.raises(_lib.LbError):                       # overlapping
+        s.set_particles([[8.0, 8.0, 8.0], [12.0, 8.0, 8.0]], radius=3.0, mass=1.0)
+    with pytest.raises(_lib.LbError):                       # too many
+        s.set_particles([[5.0, 5.0, 5.0], [15.0, 15.0, 10.0], [25.0, 5.0, 15.0]], radius=2.0, mass=1.0)
+    with pytest.raises(_lib.LbError):                       # cube wider than the grid
+        s.set_particles([[8.0, 8.0, 8.0]], radius=7.5, mass=1.0)
+    mask = np.zeros((nz, ny, nx), np.uint8)
+    mask[10, 12, 16] = 1
+    sm = Solver(nx, ny, nz, 1.0, 0.5, mask=mask, max_particles=1)
+    with pytest.raises(_lib.LbError):                       # covers a solid node of the mask
+        sm.set_particles([[16.2, 12.1, 10.3]], radius=2.5, mass=1.0)
+    s.set_particles([[8.0, 8.0, 8.0]], radius=3.0, mass=1.0)
+    s.init(dev(rA), dev(rB), dev(u))
+    with pytest.raises(_lib.LbError) as e:                  # after init
+        s.set_particles([[8.0, 8.0, 8.0]], radius=3.0, mass=1.0)
+    assert e.value.status == _lib.LB_ESTATE
+    for bad in (dict(kernel="two_pass"), dict(ckpt_every=5, ckpt_steps_max=10)):
+        with pytest.raises(Exception):
+            Solver(nx, ny, nz, 1.0, 0.5, max_particles=1, **bad)
+    with pytest.raises(Exception):                           # the box kernel needs nx % 4 == 0
+        Solver(30, ny, nz, 1.0, 0.5, max_particles=1)
+
+
+def test_full_size_256_tiled_moving_spheres():
+    """256^3 in the benchmark's launch configuration: a 32^3 periodic state
+    with one moving sphere, tiled 8 times per axis (512 spheres), evolves as
+    the oracle's 32^3 run at every site, and every sphere as the oracle's."""
+    n, p, steps, tau, G = 256, 32, 4, 1.0, 0.65
+    rA, rB, u = fields((p, p, p), 5)
+    one = dict(r=[[13.4, 15.7, 16.2]], v=[[0.23, -0.17, 0.11]], w=[[0.01, -0.02, 0.015]], radius=5.5, mass=700.0)
+    reps = n // p
+    offs = np.array([[i, j, k] for k in range(reps) for j in range(reps) for i in range(reps)], np.float64) * p
+    r = np.array(one["r"]) + offs
+    s = Solver(n, n, n, tau, G, max_particles=len(r))
+    s.set_particles(r, np.repeat(one["v"], len(r), 0), np.repeat(one["w"], len(r), 0), one["radius"], one["mass"])
+    big = lambda a: torch.tensor(np.asarray(a, np.float32), device="cuda").repeat(reps, reps, reps).contiguous()
+    s.init(big(rA), big(rB), torch.stack([big(u[a]) for a in range(3)]).contiguous())
+    s.step(steps)
+    g, owner, parts, rho0 = oracle_init((p, p, p), one, rA, rB, u)
+    for _ in range(steps):
+        g, owner = op.step(g, owner, None, parts, tau, G, rho0)
+    got = s.get_state()
+    want = ln.to_public(op.pulled(g, owner, None, parts, rho0))
+    want_t = torch.tensor(want.astype(np.float32), device="cuda").repeat(1, 1, reps, reps, reps)
+    assert float((got - want_t).abs().max()) <= 8e-7 * float(want_t.abs().max())
+    q = s.particles()
+    assert np.abs(q["r"] - np.mod(parts.r[0] + offs, n)).max() <= 1e-5
+    assert np.abs(q["F"] - parts.F[0]).max() <= 4e-6 * np.abs(parts.F).max()
