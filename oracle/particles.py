@@ -18,9 +18,13 @@ no populations. Per step, in this order:
    over links in Eq. FORCEPARTEQ and Eq. TORQUEPARTEQ with the arm r_b - r_p).
 2. The fluid step: streaming (pull) and the Shan-Chen BGK collision, with
    psi = 0 on every solid node.
-3. Newton's equations (Eq. PARDYN) by leap-frog: v += F / m, r += v,
-   w += T / I, with I = 2 m R^2 / 5 (a uniform sphere); m <= 0 marks a fixed
-   particle (its force and torque are still computed).
+3. Newton's equations (Eq. PARDYN) by leap-frog: v += (F + F_c) / m,
+   r += v, w += T / I, with I = 2 m R^2 / 5 (a uniform sphere); m <= 0 marks
+   a fixed particle (its force and torque are still computed). F_c is the
+   repulsive contact force that keeps spheres apart (the paper names a
+   Hertzian one): between two spheres whose centres are d < 2 R + delta
+   apart, k (2 R + delta - d)^(3/2) along the line of centres, pushing them
+   apart (k = 0: none).
 4. Re-meshing: nodes the moved sphere no longer covers become fluid with the
    equilibrium populations of density rho0^k and the local wall velocity;
    nodes it newly covers lose their fluid. The particle takes up the
@@ -34,7 +38,9 @@ Readings where the paper is silent (listed with the design notes):
   the link force here is the momentum the bounce exchanges with the
   exterior fluid, c_i sum_k (2 g_i^k(x) - 2 rho0^k w_i (u_b . c_i) / c_s^2);
 * the re-meshing rule (item 4) is not given in the paper; it is chosen to
-  conserve momentum exactly.
+  conserve momentum exactly;
+* the contact force's law and constants are not given; the Hertzian form
+  above with stiffness k and range delta is the reading.
 
 State (the library's write-side representation): g holds the post-collision
 populations at fluid nodes and, at solid nodes, the slots the next pull
@@ -90,7 +96,7 @@ class Particles:
     """Rigid spheres: positions r, velocities v, angular velocities w (all
     (P, 3) float64), a common radius and mass (mass <= 0: fixed)."""
 
-    def __init__(self, r, v=None, w=None, radius=5.0, mass=1.0):
+    def __init__(self, r, v=None, w=None, radius=5.0, mass=1.0, contact=(0.0, 0.0)):
         self.r = np.array(r, dtype=np.float64).reshape(-1, 3)
         P = len(self.r)
         self.v = np.zeros((P, 3)) if v is None else np.array(v, dtype=np.float64).reshape(P, 3)
@@ -99,14 +105,16 @@ class Particles:
         self.mass = float(mass)
         self.F = np.zeros((P, 3))
         self.T = np.zeros((P, 3))
+        self.Fc = np.zeros((P, 3))
+        self.contact = (float(contact[0]), float(contact[1]))
 
     @property
     def inertia(self):
         return 0.4 * self.mass * self.radius ** 2
 
     def copy(self):
-        c = Particles(self.r, self.v, self.w, self.radius, self.mass)
-        c.F, c.T = self.F.copy(), self.T.copy()
+        c = Particles(self.r, self.v, self.w, self.radius, self.mass, self.contact)
+        c.F, c.T, c.Fc = self.F.copy(), self.T.copy(), self.Fc.copy()
         return c
 
 
@@ -216,11 +224,33 @@ def collide(f, tau, G, gbody, solid):
     return out
 
 
-def advance(parts):
-    """Step 3: leap-frog with the force and torque of step 1."""
+def contact_forces(parts, box):
+    """Repulsive pair forces k (2 R + delta - d)^(3/2) along the line of
+    centres for centre distances d < 2 R + delta (minimum image)."""
+    k, delta = parts.contact
+    P = len(parts.r)
+    Fc = np.zeros((P, 3))
+    if k == 0.0:
+        return Fc
+    reach = 2.0 * parts.radius + delta
+    for i in range(P):
+        for j in range(P):
+            if i == j:
+                continue
+            d = np.array([min_image(parts.r[i][a] - parts.r[j][a], box[a]) for a in range(3)])
+            dist = np.sqrt((d * d).sum())
+            if dist < reach:
+                Fc[i] += k * (reach - dist) ** 1.5 * d / dist
+    return Fc
+
+
+def advance(parts, box):
+    """Step 3: leap-frog with the force and torque of step 1 and the contact
+    forces of the current places (box = (nx, ny, nz))."""
+    parts.Fc = contact_forces(parts, box)
     if parts.mass <= 0:
         return
-    parts.v = parts.v + parts.F / parts.mass
+    parts.v = parts.v + (parts.F + parts.Fc) / parts.mass
     parts.r = parts.r + parts.v
     parts.w = parts.w + parts.T / parts.inertia
 
@@ -278,7 +308,8 @@ def step(g, owner, mask, parts, tau, G, rho0, gbody=None):
     g, parts.F, parts.T = links_and_forces(g, owner, mask, parts, rho0)
     solid = _solid(mask, owner)
     gnew = collide(post_streaming(g), tau, G, gbody, solid)
-    advance(parts)
+    nz, ny, nx = g.shape[2:]
+    advance(parts, (nx, ny, nz))
     gnew, owner = remesh(gnew, owner, mask, parts, rho0)
     return gnew, owner
 

@@ -147,3 +147,28 @@ def test_sphere_carried_by_a_uniform_flow_moves_with_it():
     assert (owner != owner0).sum() > 10
     assert np.abs(parts.r[0] - np.mod(r0 + steps * U, (16, 12, 12))).max() <= 1e-9
     assert np.abs((g - feq) * (owner < 0)).max() <= 1e-10
+
+
+def test_contact_force_conserves_momentum_and_parts_spheres():
+    """Two spheres sent at each other head-on through fluid at rest: the
+    contact force is a central pair force (momentum is conserved with it),
+    it turns them back before they share a node, and the mirror symmetry of
+    the set-up keeps their velocities opposite."""
+    shape = (16, 16, 32)
+    rho0 = (0.5, 0.5)
+    parts = op.Particles([[11.3, 8.0, 8.0], [20.7, 8.0, 8.0]], v=[[0.06, 0, 0], [-0.06, 0, 0]], radius=3.5,
+                         mass=1000.0, contact=(0.5, 1.5))
+    owner = op.coverage(shape, parts.r, parts.radius)
+    fluid = owner < 0
+    g = np.stack([ln.equilibrium(np.full(shape, rho0[k]), np.zeros((3,) + shape)) for k in range(2)]) * fluid
+    p0 = op.fluid_momentum(g, owner, None) + parts.mass * parts.v.sum(axis=0)
+    M = op.fluid_mass(g, owner, None)
+    turned = touched = False
+    for _ in range(120):
+        g, owner = op.step(g, owner, None, parts, 1.0, 0.0, rho0)
+        p1 = op.fluid_momentum(g, owner, None) + parts.mass * parts.v.sum(axis=0)
+        assert np.abs(p1 - p0).max() <= 1e-14 * M
+        assert np.abs(parts.v[0] + parts.v[1]).max() <= 1e-12
+        turned = turned or parts.v[0][0] < 0
+        touched = touched or np.abs(parts.Fc).max() > 0
+    assert turned and touched
