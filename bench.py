@@ -186,12 +186,199 @@ def workload(name, grid=None):
         return dict(shape=(n, n, n), tau=1.0, G=0.0, rA=rho, rB=None, mask=None, model="single",
                     metric="GLUPS, 1-comp D3Q19 BGK %d^3 (the paper's single-fluid case); %% of HBM roofline" % n,
                     desc="single fluid %d^3 periodic, tau=1, rho=1+0.05U(-1,1) seed 1234, u=0" % n)
+    if name == "particles256":
+        return particle_workload(grid or 256, 0.10)
     if name == "spinodal512":
         n = 512
         rA, rB = inputs.spinodal(n, n, n, seed=1234)
         return dict(shape=(n, n, n), tau=1.0, G=0.65, rA=rA, rB=rB, mask=None,
                     desc="spinodal 512^3 periodic, tau=1, G=0.65")
     raise ValueError(name)
+
+
+def particle_workload(n, phi, seed=2112):
+    """The paper's particle setup (case 3): spheres of radius 5.5 at random,
+    non-overlapping places filling the volume fraction phi, at rest, with the
+    mass of silica in a fluid of density 1 (2.2 times the sphere's volume),
+    in the headline spinodal fill."""
+    from paper_2112_08264_gb300 import inputs
+    R = 5.5
+    vol = 4.0 / 3.0 * np.pi * R ** 3
+    count = max(1, int(round(phi * n ** 3 / vol)))
+    mask, centres = inputs.colloid_mask(n, n, n, n_spheres=count, radius=R, seed=seed)
+    rA, rB = inputs.spinodal(n, n, n, seed=1234)
+    return dict(shape=(n, n, n), tau=1.0, G=0.65, rA=rA, rB=rB, mask=None, model="particles",
+                spheres=dict(r=centres, radius=R, mass=2.2 * vol, contact=(10.0, 1.0)), phi=phi,
+                fluid=float((mask == 0).mean()),
+                metric="GLUPS, 2-comp D3Q19 Shan-Chen %d^3 with %d moving spheres R = 5.5 (volume fraction %g, "
+                       "the paper's particle case); %% of HBM roofline" % (n, count, phi),
+                desc="spinodal %d^3 (seed 1234), tau=1, G=0.65; %d spheres R=5.5 at rest, random places "
+                     "(seed %d, gaps >= 1), mass 2.2 x volume, contact k = 10 within 1 node" % (n, count, seed))
+
+
+def time_particles(W, prec, steps, warmup):
+    """Device-resident timing of the step with moving spheres (CUDA events on
+    the solver's stream around exactly `steps` steps)."""
+    import torch
+    from paper_2112_08264_gb300 import Solver
+    nx, ny, nz = W["shape"]
+    sp = W["spheres"]
+    s = Solver(nx, ny, nz, W["tau"], W["G"], prec=prec, max_particles=len(sp["r"]))
+    s.set_particles(sp["r"], radius=sp["radius"], mass=sp["mass"], contact=sp["contact"])
+    s.init(torch.tensor(W["rA"], dtype=torch.float32, device="cuda"),
+           torch.tensor(W["rB"], dtype=torch.float32, device="cuda"))
+    s.step(warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(s.stream):
+        e0.record(s.stream)
+        s.step(steps)
+        e1.record(s.stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    info, st = s.launch_info(), s.stats()
+    p = s.particles()          # raises if spheres met or ran faster than a node per step
+    s.close()
+    torch.cuda.synchronize()
+    return ms, info, st, p
+
+
+def e2e_particles(W, prec, steps):
+    """Host fields and sphere places -> pinned H2D -> lb_particles_set ->
+    lb_init -> steps -> moments and spheres -> D2H, timed on the host (the
+    context and its workspace are made before the timed region)."""
+    import torch
+    from paper_2112_08264_gb300 import Solver
+    nx, ny, nz = W["shape"]
+    sp = W["spheres"]
+    hA = torch.from_numpy(W["rA"].astype(np.float32)).pin_memory()
+    hB = torch.from_numpy(W["rB"].astype(np.float32)).pin_memory()
+
+    def run(k):
+        s = Solver(nx, ny, nz, W["tau"], W["G"], prec=prec, max_particles=len(sp["r"]))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(s.stream):
+            dA = hA.to("cuda", non_blocking=True)
+            dB = hB.to("cuda", non_blocking=True)
+            s.set_particles(sp["r"], radius=sp["radius"], mass=sp["mass"], contact=sp["contact"])
+            s.init(dA, dB)
+            s.step(k)
+            oA, oB, ou = s.moments()
+            out = [x.cpu() for x in (oA, oB, ou)]
+        p = s.particles()
+        t1 = time.perf_counter()
+        s.close()
+        del out, p
+        return t1 - t0
+
+    run(3)   # warm
+    dt = run(steps)
+    n = nx * ny * nz
+    return dt, 2 * n * 4 + 3 * 8 * len(sp["r"]), 5 * n * 4 + 15 * 8 * len(sp["r"])
+
+
+def particle_oracle_sample(W, n_xy=64, nz_s=24):
+    """The particle oracle on a periodic 64 x 64 x 24 sample of the workload:
+    the same fill and sphere size at the same volume fraction."""
+    from oracle import particles as op
+    from paper_2112_08264_gb300 import inputs
+    sp = W["spheres"]
+    R = sp["radius"]
+    count = max(1, int(round(W["phi"] * n_xy * n_xy * nz_s / (4.0 / 3.0 * np.pi * R ** 3))))
+    _, centres = inputs.colloid_mask(n_xy, n_xy, nz_s, n_spheres=count, radius=R, seed=7)
+    rA, rB = inputs.spinodal(n_xy, n_xy, nz_s, seed=1234)
+    parts = op.Particles(centres, radius=R, mass=sp["mass"], contact=sp["contact"])
+    owner = op.coverage((nz_s, n_xy, n_xy), parts.r, R)
+    fluid = owner < 0
+    rho0 = (rA[fluid].mean(), rB[fluid].mean())
+    state = [op.init(rA, rB, None, None, owner), owner]
+
+    def step():
+        state[0], state[1] = op.step(state[0], state[1], None, parts, W["tau"], W["G"], rho0)
+    return step, n_xy * n_xy * nz_s, "%d spheres in a %dx%dx%d periodic sample" % (count, n_xy, n_xy, nz_s)
+
+
+def main_particles(args, W, world, rank, local):
+    """The step with moving spheres: same JSON contract as the other lines."""
+    nx, ny, nz = W["shape"]
+    N = nx * ny * nz
+    peak, peak_kind = measured_peaks()
+    barrier(world)
+    with ClockSampler(local) as clk:
+        ms, info, st, p = time_particles(W, args.prec, args.steps, args.warmup)
+    clocks = clk.summary()
+    if not clocks_ok(clocks):
+        with ClockSampler(local) as clk:
+            ms, info, st, p = time_particles(W, args.prec, args.steps, args.warmup)
+        clocks = clk.summary()
+        clocks["remeasured"] = True
+    barrier(world)
+    glups, step_s = replica_throughput(ms, args.steps, N, world)
+    fluid = W["fluid"]
+    alg_bytes = fluid * BYTES_PER_SITE[args.prec] + 4
+    achieved = alg_bytes * N / step_s / 1e9
+    line = {
+        "metric": W["metric"], "value": glups, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
+        # the paper's particle runs (Table partic: V100 0.484 / 0.446 / 0.299 GLUPS at 0.1 / 1 / 10 %) use
+        # its colour-gradient fluid with contact and lubrication forces: context, not this workload
+        "vs_baseline": None, "dtype": DTYPE_TAG[args.prec], "data": "synthetic",
+        "config": {"workload": W["desc"], "grid": [nx, ny, nz], "prec": args.prec, "kernel": "fused",
+                   "spheres": len(W["spheres"]["r"]), "volume_fraction": W["phi"],
+                   "parallelism": "replicas" if world > 1 else "single-gpu",
+                   "l2": "state %.2f GB per buffer > 129 MB L2; no flush needed"
+                         % (38 * N * (BYTES_PER_SITE[args.prec] / 76) / 1e9),
+                   "launch": info},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": peak_kind, "algorithmic_bytes_per_site": alg_bytes,
+                     "timed": "the whole step (%d launches: sphere links, step kernel, leap-frog, two re-meshing "
+                              "passes, flags)" % info["launches_per_step"],
+                     "traffic": None},
+        "gpu_launches": args.steps * info["launches_per_step"],
+        "fluid_glups": glups * fluid,
+        "clocks": clocks,
+        "conserved_totals": [float(x) for x in st],
+        "spheres_after": {"max_speed": float(np.abs(p["v"]).max()), "max_force": float(np.abs(p["F"]).max())},
+        "paper_context": {"V100_GLUPS": {"0.1%": 0.484, "1%": 0.446, "10%": 0.299}},
+    }
+    if rank == 0 and not args.no_e2e:
+        dt, h2d, d2h = e2e_particles(W, args.prec, args.steps)
+        line["e2e"] = {"value": N * args.steps / dt / 1e9, "unit": "GLUPS", "h2d_bytes_per_step": h2d / args.steps,
+                       "d2h_bytes_per_step": d2h / args.steps,
+                       "what": "host fields + sphere places -> pinned H2D -> lb_particles_set -> lb_init -> %d "
+                               "steps -> moments + spheres -> D2H" % args.steps}
+    if rank == 0 and not args.no_variants:
+        var = {}
+        for prec in ("fp16",):
+            if prec == args.prec:
+                continue
+            vms, vinfo, _, _ = time_particles(W, prec, args.steps, args.warmup)
+            var["%s_phi%g" % (prec, W["phi"])] = {"GLUPS": N / (vms / 1e3 / args.steps) / 1e9,
+                                                   "ms_per_step": vms / args.steps}
+        for phi in (0.01, 0.001):
+            Wv = particle_workload(nx, phi)
+            vms, _, _, _ = time_particles(Wv, args.prec, args.steps, args.warmup)
+            var["%s_phi%g" % (args.prec, phi)] = {"GLUPS": N / (vms / 1e3 / args.steps) / 1e9,
+                                                  "ms_per_step": vms / args.steps, "spheres": len(Wv["spheres"]["r"])}
+        line["variants"] = var
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        step, sites, what = particle_oracle_sample(W)
+        t0 = time.perf_counter()
+        k = 0
+        while time.perf_counter() - t0 < 10.0 or k < 2:
+            step()
+            k += 1
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": sites * k / dt / 1e9, "unit": "GLUPS", "cores": 1, "kind": "oracle",
+                                "sample": "%d FP64 particle-oracle steps (numpy, one thread), %s (%.1f s)"
+                                          % (k, what, dt)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
 
 
 def time_device(W, prec, kernel, steps, warmup, events_per_step=False):
@@ -367,6 +554,13 @@ def main_reference(args, world, rank):
     elif W.get("model") == "single":
         f, step, nzs, _ = single_oracle_sample(W, per_step_budget=per_step)
         cores = 1
+    elif W.get("model") == "particles":
+        pstep, sites, what = particle_oracle_sample(W)
+        f, nzs, cores = None, sites / (nx * ny), 1
+
+        def step(_):
+            pstep()
+            return None
     else:
         rA, rB, nzs, _, cores = oracle_sample(W["shape"], W["tau"], W["G"], None, per_step_budget=per_step)
         f = oracle.init(rA, rB)
@@ -379,6 +573,8 @@ def main_reference(args, world, rank):
     dt = time.perf_counter() - t0
     glups = nx * ny * nzs * args.steps / dt / 1e9
     sample = "each step: one FP64 oracle step on a %dx%dx%d periodic slab of the workload" % (nx, ny, nzs)
+    if W.get("model") == "particles":
+        sample = "each step: one FP64 particle-oracle step (numpy, one thread), " + what
     line = {"impl": "reference", "metric": W.get("metric", METRIC), "value": glups, "unit": "GLUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -527,7 +723,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="spinodal256",
-                    choices=["spinodal256", "colloid256", "orderparam256", "cg256", "single256", "spinodal512"])
+                    choices=["spinodal256", "colloid256", "orderparam256", "cg256", "single256", "particles256",
+                             "spinodal512"])
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--kernel", default="fused", choices=["fused", "two_pass"])
     ap.add_argument("--grid", type=int, default=None, help="override the spinodal grid size (profiling)")
@@ -549,6 +746,8 @@ def main():
     W = workload(args.config, args.grid)
     if W.get("model") == "single":
         return main_single(args, W, world, rank, local)
+    if W.get("model") == "particles":
+        return main_particles(args, W, world, rank, local)
     nx, ny, nz = W["shape"]
     N = nx * ny * nz
     peak, peak_kind = measured_peaks()

@@ -209,6 +209,15 @@ lb_status lb_launch_info(const lb_ctx* ctx, int* launches_per_step, int* grid_bl
 lb_status lb_particles_set(lb_ctx* ctx, int n, const double* r, const double* v, const double* w, double radius,
                            double mass);
 
+/* Contact force between spheres (the paper's spheres repel on contact with a
+ * Hertzian force; its constants are not given): two spheres whose centres
+ * are d < 2 radius + range apart (periodic) are pushed apart along the line
+ * of centres by stiffness (2 radius + range - d)^(3/2) each, added to the
+ * force of the leap-frog update. stiffness = 0 (the default) turns it off.
+ * Any time after lb_create; LB_EINVAL for negative or non-finite values,
+ * LB_ESTATE without room for spheres. Host function. */
+lb_status lb_particles_contact(lb_ctx* ctx, double stiffness, double range);
+
 /* The spheres after the last step, into HOST arrays of 3n doubles (any may
  * be NULL): r, v, w as above, and F, T = the force and torque of the last
  * step's links. LB_ESTATE (arrays still filled) when a step met spheres that

@@ -103,10 +103,18 @@ cudaError_t launch_reflect(int prec, void* g_state, const uint32_t* flags, const
 // than one node per step).
 struct Spheres {
     double *r = nullptr, *v = nullptr, *w = nullptr, *F = nullptr, *T = nullptr;
+    double* Fc = nullptr;   // contact forces
     int* owner = nullptr;
     int* err = nullptr;
+    int* moved = nullptr;   // per sphere: 1 when the last re-meshing changed a node
+    // per sphere: centre at the last full re-meshing pass (3 doubles) and the
+    // distance from there of the node nearest to its surface; a sphere that
+    // has moved less than that changes no node
+    double* ref = nullptr;
+    float* margin = nullptr;
     int n = 0;
     double radius = 0.0, mass = 0.0, inertia = 0.0;
+    double contact_k = 0.0, contact_range = 0.0;   // k (2R + range - d)^(3/2) for d < 2R + range
     int half = 0;   // box half-width around a centre: ceil(radius) + 2
 };
 // Moving-wall bounce-back into the solid slots of `state` and, when

@@ -97,8 +97,9 @@ Layout make_layout(int nx, int ny, int nz, const lb_options& o) {
     L.red_out = off; off += align256(kRedVals * 8);
     if (o.max_particles > 0) {
         L.owner = off; off += align256(N * 4);   // sphere covering each site
-        // r, v, w, F, T (3 doubles each per sphere) and the error word
-        L.spheres = off; off += align256((size_t)o.max_particles * 15 * 8 + 8);
+        // r, v, w, F, T, F_c, ref (3 doubles each per sphere), the error word, and per sphere a moved
+        // flag and a margin
+        L.spheres = off; off += align256((size_t)o.max_particles * 21 * 8 + 8 + (size_t)o.max_particles * 8);
     }
     if (o.ckpt_every > 0) {
         L.ckpt_slots = (size_t)(o.ckpt_steps_max / o.ckpt_every) + 1;
@@ -302,7 +303,11 @@ lb_status lb_create(int nx, int ny, int nz, float tau, float G, const uint8_t* m
         S.w = a + 2 * P3;
         S.F = a + 3 * P3;
         S.T = a + 4 * P3;
-        S.err = reinterpret_cast<int*>(a + 5 * P3);
+        S.Fc = a + 5 * P3;
+        S.ref = a + 6 * P3;
+        S.err = reinterpret_cast<int*>(a + 7 * P3);
+        S.moved = S.err + 2;   // 8-byte error slot, then the flags
+        S.margin = reinterpret_cast<float*>(S.moved + o.max_particles);
         S.owner = reinterpret_cast<int*>(c->ws + L.owner);
         S.n = 0;
         if (!mask) c->links.sites = reinterpret_cast<const uint32_t*>(c->ws + L.links);   // no static links
@@ -481,7 +486,9 @@ lb_status lb_launch_info(const lb_ctx* c, int* launches, int* blocks, int* threa
     const int k = c->opt.kernel;
     // a masked step adds the write-side bounce-back passes (launch_reflect)
     // spheres: their links, and when they move the update, two re-meshing passes and the flags
-    const int sph = !c->particles || c->sph.n == 0 ? 0 : (c->sph.mass > 0.0 ? 5 : 1);
+    const int sph = !c->particles || c->sph.n == 0
+                        ? 0
+                        : (c->sph.mass > 0.0 ? 5 + (c->sph.contact_k != 0.0 ? 1 : 0) : 1);
     if (launches) *launches = (k == LB_KERNEL_TWO_PASS ? 2 : 1) + reflect_launches(c) + sph;
     if (blocks)
         *blocks = k == LB_KERNEL_FUSED ? c->plan.ncols * c->plan.R * c->plan.zsplit
@@ -500,7 +507,7 @@ lb_status lb_particles_set(lb_ctx* c, int n, const double* r, const double* v, c
     const int half = (int)std::ceil(radius) + 2;
     if (2 * (half + 1) + 1 > std::min(c->g.nx, std::min(c->g.ny, c->g.nz))) return LB_EINVAL;
     const int dims[3] = {c->g.nx, c->g.ny, c->g.nz};
-    std::vector<double> h(15 * (size_t)n, 0.0);   // r, v, w, F, T
+    std::vector<double> h(18 * (size_t)n, 0.0);   // r, v, w, F, T, F_c
     for (int q = 0; q < n; ++q)
         for (int a = 0; a < 3; ++a) {
             const double x = r[3 * q + a];
@@ -526,10 +533,10 @@ lb_status lb_particles_set(lb_ctx* c, int n, const double* r, const double* v, c
     const size_t P3 = (size_t)c->opt.max_particles * 3;
     cudaError_t e = cudaSuccess;
     if (n > 0) {
-        const double* src[5] = {h.data(), h.data() + 3 * (size_t)n, h.data() + 6 * (size_t)n,
-                                h.data() + 9 * (size_t)n, h.data() + 12 * (size_t)n};
-        double* dst[5] = {S.r, S.v, S.w, S.F, S.T};
-        for (int k = 0; k < 5 && e == cudaSuccess; ++k)
+        const double* src[6] = {h.data(), h.data() + 3 * (size_t)n, h.data() + 6 * (size_t)n,
+                                h.data() + 9 * (size_t)n, h.data() + 12 * (size_t)n, h.data() + 15 * (size_t)n};
+        double* dst[6] = {S.r, S.v, S.w, S.F, S.T, S.Fc};
+        for (int k = 0; k < 6 && e == cudaSuccess; ++k)
             e = cudaMemcpyAsync(dst[k], src[k], 3 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
     }
     (void)P3;
@@ -550,6 +557,15 @@ lb_status lb_particles_set(lb_ctx* c, int n, const double* r, const double* v, c
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         return e == cudaSuccess ? LB_EINVAL : cuda_status("particles_set", e);
     }
+    return LB_OK;
+}
+
+lb_status lb_particles_contact(lb_ctx* c, double stiffness, double range) {
+    if (!c) return LB_EINVAL;
+    if (!c->particles) return LB_ESTATE;
+    if (!std::isfinite(stiffness) || stiffness < 0.0 || !std::isfinite(range) || range < 0.0) return LB_EINVAL;
+    c->sph.contact_k = stiffness;
+    c->sph.contact_range = range;
     return LB_OK;
 }
 

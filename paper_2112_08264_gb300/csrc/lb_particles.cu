@@ -28,7 +28,7 @@ __device__ __forceinline__ int wrapn(int a, int n) {
     return a < 0 ? a + n : a;
 }
 
-// minimum-image displacement along one axis of period n
+// minimum-image displacement along one axis of period n (general form)
 __device__ __forceinline__ double min_image(double d, int n) {
     return __dsub_rn(d, __dmul_rn((double)n, rint(__ddiv_rn(d, (double)n))));
 }
@@ -37,44 +37,94 @@ __device__ __forceinline__ double norm2(double a, double b, double c) {
     return __dadd_rn(__dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b)), __dmul_rn(c, c));
 }
 
-// The cube of sites of one sphere: site b of side^3 at unwrapped coordinates
-// lo + (bx, by, bz).
+// The cube of sites of one sphere, centred on floor(c): site b of side^3
+// has unwrapped coordinates u = lo + (bx, by, bz) and grid coordinates
+// x = u + n m (m the wrap count). Its half-width keeps |u - c| below n / 2,
+// so the minimum-image displacement of x from c is (x - c) - n m, rounded
+// as that plain evaluation rounds it (no division).
 struct Cube {
     int lo[3];
     int side;
+    int base[3];    // floor(c)
+    float frac[3];  // c - floor(c)
     __device__ Cube(const double* c, int half) {
         side = 2 * half + 1;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) lo[a] = (int)floor(c[a]) - half;
+        for (int a = 0; a < 3; ++a) {
+            const double f = floor(c[a]);
+            base[a] = (int)f;
+            frac[a] = (float)(c[a] - f);
+            lo[a] = base[a] - half;
+        }
     }
     __device__ int count() const { return side * side * side; }
-    // site b as wrapped grid coordinates
-    __device__ void at(int b, const Geom& g, int (&u)[3]) const {
-        u[0] = wrapn(lo[0] + b % side, g.nx);
-        u[1] = wrapn(lo[1] + (b / side) % side, g.ny);
-        u[2] = wrapn(lo[2] + b / (side * side), g.nz);
+    __device__ void at(int b, const Geom& g, int (&u)[3], int (&x)[3]) const {
+        u[0] = lo[0] + b % side;
+        u[1] = lo[1] + (b / side) % side;
+        u[2] = lo[2] + b / (side * side);
+        x[0] = wrapn(u[0], g.nx);
+        x[1] = wrapn(u[1], g.ny);
+        x[2] = wrapn(u[2], g.nz);
+    }
+    // approximate squared distance from the centre (FP32, for shell tests)
+    __device__ float dist2(const int (&u)[3], float (&d)[3]) const {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) d[a] = (float)(u[a] - base[a]) - frac[a];
+        return d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
     }
 };
 
-__device__ __forceinline__ uint32_t site_of(const int (&u)[3], const Geom& g) {
-    return (uint32_t)wrapn(u[0], g.nx) + (uint32_t)g.nx * ((uint32_t)wrapn(u[1], g.ny) +
-                                                          (uint32_t)g.ny * (uint32_t)wrapn(u[2], g.nz));
+// exact minimum-image displacement of grid coordinate x (unwrapped u) from c
+__device__ __forceinline__ double disp(int x, int u, double c, int n) {
+    const int m = (x - u) / n;
+    return __dsub_rn(__dsub_rn((double)x, c), (double)(n * m));
 }
 
-__device__ __forceinline__ void cross(const double (&a)[3], const double (&b)[3], double (&o)[3]) {
+// Is the site within radius of the centre? Far from the sphere's surface the
+// FP32 distance decides; near it, the exact FP64 test (the oracle's rule).
+__device__ __forceinline__ bool covered(const Cube& cube, const int (&u)[3], const int (&x)[3], float r2f,
+                                        const double* c, double R2, const Geom& g) {
+    const float R2f = (float)R2;
+    if (r2f < 0.99f * R2f) return true;
+    if (r2f > 1.01f * R2f) return false;
+    return norm2(disp(x[0], u[0], c[0], g.nx), disp(x[1], u[1], c[1], g.ny), disp(x[2], u[2], c[2], g.nz)) <= R2;
+}
+
+// Has sphere q moved less than its margin since its last full re-meshing
+// pass? Then no node can have changed (each node's distance to the centre
+// changes by at most the displacement).
+__device__ __forceinline__ bool within_margin(const Spheres& A, int q, const Geom& g) {
+    const int n[3] = {g.nx, g.ny, g.nz};
+    float d2 = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float d = (float)(A.r[3 * q + a] - A.ref[3 * q + a]);
+        d -= (float)n[a] * rintf(d / (float)n[a]);
+        d2 += d * d;
+    }
+    const float m = A.margin[q] - 1e-4f;   // FP32 slack
+    return m > 0.f && d2 < m * m;
+}
+
+__device__ __forceinline__ uint32_t site_of(const int (&x)[3], const Geom& g) {
+    return (uint32_t)x[0] + (uint32_t)g.nx * ((uint32_t)x[1] + (uint32_t)g.ny * (uint32_t)x[2]);
+}
+
+template <typename T>
+__device__ __forceinline__ void cross(const T (&a)[3], const T (&b)[3], T (&o)[3]) {
     o[0] = a[1] * b[2] - a[2] * b[1];
     o[1] = a[2] * b[0] - a[0] * b[2];
     o[2] = a[0] * b[1] - a[1] * b[0];
 }
 
 // Fixed-tree block sum of NV doubles per thread; thread 0 gets the totals.
-template <int NV>
+template <int NV, int NT = kPT>
 __device__ void block_sum(double (&v)[NV]) {
-    __shared__ double red[NV][kPT];
+    __shared__ double red[NV][NT];
 #pragma unroll
     for (int k = 0; k < NV; ++k) red[k][threadIdx.x] = v[k];
     __syncthreads();
-    for (int h = kPT / 2; h > 0; h >>= 1) {
+    for (int h = NT / 2; h > 0; h >>= 1) {
         if ((int)threadIdx.x < h)
 #pragma unroll
             for (int k = 0; k < NV; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + h];
@@ -84,73 +134,152 @@ __device__ void block_sum(double (&v)[NV]) {
     for (int k = 0; k < NV; ++k) v[k] = red[k][0];
 }
 
-__device__ __forceinline__ void load3(const double* a, int q, double (&o)[3]) {
+template <typename T>
+__device__ __forceinline__ void load3(const double* a, int q, T (&o)[3]) {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) o[k] = a[3 * q + k];
+    for (int k = 0; k < 3; ++k) o[k] = (T)a[3 * q + k];
 }
 
 // Links from fluid nodes into sphere q: slot opp(i) of the covered node
 // x + c_i takes g_i(x) - 2 rho0^k w_i (u_b . c_i) / c_s^2, and the link adds
 // c_i sum_k (2 g_i^k(x) - 2 rho0^k w_i (u_b . c_i) / c_s^2) to the force and
-// (r_b - r) x that to the torque.
+// (r_b - r) x that to the torque. The exchanged momentum splits into the
+// rest part c_i 2 w_i (rho0^A + rho0^B), large and cancelling over the
+// surface, and a small deviation part. With 36 w_i integer and the link
+// midpoint r_b = x + c_i / 2, the rest part's force and torque are exact
+// integer sums of the link geometry, scaled once per sphere in FP64; the
+// deviation part and the wall velocity are FP32 per link (as the state is),
+// summed in FP64 across the block. Only the shell of sites between R - 1/2
+// and R + 2 from the centre can be linked to the sphere.
 template <typename S>
 __global__ void __launch_bounds__(kPT) sphere_links_kernel(S* __restrict__ st, const uint32_t* __restrict__ flags,
                                                           Spheres A, int forces, Geom g, Phys p) {
     const int q = blockIdx.x;
-    double c[3], v[3], w[3];
+    double c[3];
+    float v[3], w[3];
     load3(A.r, q, c);
     load3(A.v, q, v);
     load3(A.w, q, w);
     const Cube cube(c, A.half);
-    double acc[6] = {0, 0, 0, 0, 0, 0};
+    const float lo2 = (float)((A.radius - 0.5) * (A.radius - 0.5));
+    const float hi2 = (float)((A.radius + 2.0) * (A.radius + 2.0));
+    int gF[3] = {0, 0, 0}, gT[3] = {0, 0, 0};   // sum 36 w_i c_i, sum 36 w_i (2 (u - base) + c_i) x c_i
+    float dF[3] = {0.f, 0.f, 0.f}, dT[3] = {0.f, 0.f, 0.f};
     for (int b = threadIdx.x; b < cube.count(); b += kPT) {
-        int u[3];
-        cube.at(b, g, u);
-        const uint32_t s = site_of(u, g);
+        int u[3], x[3];
+        cube.at(b, g, u, x);
+        float d[3];
+        const float r2 = cube.dist2(u, d);
+        if (r2 <= lo2 || r2 > hi2) continue;
+        const uint32_t s = site_of(x, g);
         const uint32_t fl = __ldg(flags + s);
         if ((fl & kSolid) || !(fl & kNbSolidMask)) continue;
+        const int xm = wrap_dec(x[0], g.nx), xp = wrap_inc(x[0], g.nx);
+        const int ym = wrap_dec(x[1], g.ny), yp = wrap_inc(x[1], g.ny);
+        const int zm = wrap_dec(x[2], g.nz), zp = wrap_inc(x[2], g.nz);
+        const int h0[3] = {2 * (u[0] - cube.base[0]), 2 * (u[1] - cube.base[1]), 2 * (u[2] - cube.base[2])};
         static_for<1, Q>([&](auto I) {
             constexpr int i = decltype(I)::value;
+            constexpr int cx = Vel<i>::x, cy = Vel<i>::y, cz = Vel<i>::z;
+            constexpr int w36 = Vel<i>::c2 == 1 ? 2 : 1;
             if (!(fl & (1u << Vel<i>::opp))) return;   // x + c_i is fluid
-            const int t3[3] = {u[0] + Vel<i>::x, u[1] + Vel<i>::y, u[2] + Vel<i>::z};
+            const int t3[3] = {cx > 0 ? xp : (cx < 0 ? xm : x[0]), cy > 0 ? yp : (cy < 0 ? ym : x[1]),
+                               cz > 0 ? zp : (cz < 0 ? zm : x[2])};
             const uint32_t t = site_of(t3, g);
             if (A.owner[t] != q + 1) return;
-            const double arm[3] = {min_image(((double)u[0] + 0.5 * Vel<i>::x) - c[0], g.nx),
-                                   min_image(((double)u[1] + 0.5 * Vel<i>::y) - c[1], g.ny),
-                                   min_image(((double)u[2] + 0.5 * Vel<i>::z) - c[2], g.nz)};
-            double wa[3];
+            const float arm[3] = {d[0] + 0.5f * cx, d[1] + 0.5f * cy, d[2] + 0.5f * cz};
+            float wa[3];
             cross(w, arm, wa);
-            const double cu = 3.0 * (Vel<i>::x * (v[0] + wa[0]) + Vel<i>::y * (v[1] + wa[1]) +
-                                     Vel<i>::z * (v[2] + wa[2]));
+            const float cu = 3.0f * (cx * (v[0] + wa[0]) + cy * (v[1] + wa[1]) + cz * (v[2] + wa[2]));
             float dA, dB;
             Store<S>::ld2(st + pidx(0, i, s), dA, dB);
-            const double bA = 2.0 * (double)p.rho0[0] * wgt_d<i>() * cu;
-            const double bB = 2.0 * (double)p.rho0[1] * wgt_d<i>() * cu;
-            Store<S>::st2(st + pidx(0, Vel<i>::opp, t), dA - (float)bA, dB - (float)bB);
+            const float bA = 2.0f * p.rho0[0] * wgt<i>() * cu;
+            const float bB = 2.0f * p.rho0[1] * wgt<i>() * cu;
+            Store<S>::st2(st + pidx(0, Vel<i>::opp, t), dA - bA, dB - bB);
             if (!forces) return;
-            const double ex = 2.0 * ((double)dA + wgt_d<i>() * (double)p.rho0[0]) - bA +
-                              2.0 * ((double)dB + wgt_d<i>() * (double)p.rho0[1]) - bB;
-            const double F[3] = {Vel<i>::x * ex, Vel<i>::y * ex, Vel<i>::z * ex};
-            double Tq[3];
+            const int h[3] = {h0[0] + cx, h0[1] + cy, h0[2] + cz};
+            gF[0] += w36 * cx;
+            gF[1] += w36 * cy;
+            gF[2] += w36 * cz;
+            gT[0] += w36 * (h[1] * cz - h[2] * cy);
+            gT[1] += w36 * (h[2] * cx - h[0] * cz);
+            gT[2] += w36 * (h[0] * cy - h[1] * cx);
+            const float ex = 2.0f * (dA + dB) - (bA + bB);
+            const float F[3] = {cx * ex, cy * ex, cz * ex};
+            float Tq[3];
             cross(arm, F, Tq);
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                acc[a] += F[a];
-                acc[3 + a] += Tq[a];
+                dF[a] += F[a];
+                dT[a] += Tq[a];
             }
         });
     }
     if (!forces) return;
+    double acc[12];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        acc[a] = gF[a];
+        acc[3 + a] = gT[a];
+        acc[6 + a] = dF[a];
+        acc[9 + a] = dT[a];
+    }
     block_sum(acc);
-    if (threadIdx.x == 0)
+    if (threadIdx.x == 0) {
+        const double r36 = 2.0 * ((double)p.rho0[0] + (double)p.rho0[1]) / 36.0;
+        const double fr[3] = {c[0] - cube.base[0], c[1] - cube.base[1], c[2] - cube.base[2]};
+        const double Fr[3] = {r36 * acc[0], r36 * acc[1], r36 * acc[2]};
+        double frF[3];
+        cross(fr, Fr, frF);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            A.F[3 * q + a] = acc[a];
-            A.T[3 * q + a] = acc[3 + a];
+            A.F[3 * q + a] = Fr[a] + acc[6 + a];
+            A.T[3 * q + a] = 0.5 * r36 * acc[3 + a] - frF[a] + acc[9 + a];
         }
+    }
 }
 
-// Leap-frog: v += F / m, r += v (wrapped into the box), w += T / I.
+// Contact forces: k (2R + range - d)^(3/2) along the line of centres for
+// every other sphere whose centre is d < 2R + range away (minimum image),
+// pushing the two apart. One block per sphere, partners split over its
+// threads in index order; an FP32 distance test skips the far ones.
+constexpr int kCT = 128;
+__global__ void __launch_bounds__(kCT) sphere_contact_kernel(Spheres A, Geom g) {
+    const int q = blockIdx.x;
+    const int n[3] = {g.nx, g.ny, g.nz};
+    const double reach = 2.0 * A.radius + A.contact_range;
+    const float near2 = (float)((reach + 0.5) * (reach + 0.5));
+    double c[3];
+    float cf[3];
+    load3(A.r, q, c);
+    load3(A.r, q, cf);
+    double F[3] = {0, 0, 0};
+    for (int j = threadIdx.x; j < A.n; j += kCT) {
+        if (j == q) continue;
+        float e2 = 0.f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float d = cf[a] - (float)A.r[3 * j + a];
+            d -= (float)n[a] * rintf(d / (float)n[a]);
+            e2 += d * d;
+        }
+        if (e2 >= near2) continue;
+        double d[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) d[a] = min_image(c[a] - A.r[3 * j + a], n[a]);
+        const double dist = sqrt(norm2(d[0], d[1], d[2]));
+        if (!(dist < reach)) continue;
+        const double f = A.contact_k * pow(reach - dist, 1.5);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) F[a] += f * d[a] / dist;
+    }
+    block_sum<3, kCT>(F);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) A.Fc[3 * q + a] = F[a];
+}
+
+// Leap-frog: v += (F + F_c) / m, r += v (wrapped into the box), w += T / I.
 __global__ void sphere_update_kernel(Spheres A, Geom g) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= A.n || !(A.mass > 0.0)) return;
@@ -158,7 +287,8 @@ __global__ void sphere_update_kernel(Spheres A, Geom g) {
     bool fast = false;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const double v = __dadd_rn(A.v[3 * q + a], __ddiv_rn(A.F[3 * q + a], A.mass));
+        const double v = __dadd_rn(A.v[3 * q + a],
+                                   __ddiv_rn(__dadd_rn(A.F[3 * q + a], A.Fc[3 * q + a]), A.mass));
         double r = __dadd_rn(A.r[3 * q + a], v);
         // r mod n (the remainder of an exact division, then into [0, n))
         const double m = fmod(r, (double)n[a]);
@@ -173,7 +303,8 @@ __global__ void sphere_update_kernel(Spheres A, Geom g) {
 
 // Re-meshing, first pass: nodes sphere q covered and no longer covers become
 // fluid with f^eq(rho0^k, u_b) at the wall velocity there; the sphere loses
-// that momentum (and its moment).
+// that momentum (and its moment). A sphere moves at most one node per step,
+// so such nodes lie within R + 2 of the new centre.
 template <typename S>
 __global__ void __launch_bounds__(kPT) sphere_uncover_kernel(S* __restrict__ st, Spheres A, Geom g, Phys p) {
     const int q = blockIdx.x;
@@ -183,17 +314,25 @@ __global__ void __launch_bounds__(kPT) sphere_uncover_kernel(S* __restrict__ st,
     load3(A.w, q, w);
     const Cube cube(c, A.half);
     const double R2 = __dmul_rn(A.radius, A.radius);
+    const float in2 = (float)((A.radius - 2.0) * (A.radius - 2.0));
     const double r0 = (double)p.rho0[0] + (double)p.rho0[1];
+    if (threadIdx.x == 0) A.moved[q] = 0;
+    if (within_margin(A, q, g)) return;   // the whole block: no node changed
+    __syncthreads();
     double acc[6] = {0, 0, 0, 0, 0, 0};
     for (int b = threadIdx.x; b < cube.count(); b += kPT) {
-        int u[3];
-        cube.at(b, g, u);
-        const uint32_t s = site_of(u, g);
+        int u[3], x[3];
+        cube.at(b, g, u, x);
+        float df[3];
+        const float r2 = cube.dist2(u, df);
+        if (A.radius > 2.0 && r2 < in2) continue;   // deep inside: still covered
+        const uint32_t s = site_of(x, g);
         if (A.owner[s] != q + 1) continue;
-        const double arm[3] = {min_image((double)u[0] - c[0], g.nx), min_image((double)u[1] - c[1], g.ny),
-                               min_image((double)u[2] - c[2], g.nz)};
-        if (norm2(arm[0], arm[1], arm[2]) <= R2) continue;   // still covered
+        if (covered(cube, u, x, r2, c, R2, g)) continue;
         A.owner[s] = 0;
+        A.moved[q] = 1;
+        const double arm[3] = {disp(x[0], u[0], c[0], g.nx), disp(x[1], u[1], c[1], g.ny),
+                               disp(x[2], u[2], c[2], g.nz)};
         double ub[3];
         cross(w, arm, ub);
 #pragma unroll
@@ -226,7 +365,7 @@ __global__ void __launch_bounds__(kPT) sphere_uncover_kernel(S* __restrict__ st,
 // Re-meshing, second pass (and placement when !absorb): nodes sphere q now
 // covers and did not take its fluid's momentum (and moment); their
 // populations are cleared. A node held by another sphere or by the mask is
-// an error.
+// an error. After a move such nodes lie beyond R - 2 from the centre.
 template <typename S>
 __global__ void __launch_bounds__(kPT) sphere_cover_kernel(S* __restrict__ st, const uint8_t* __restrict__ mask,
                                                           Spheres A, int absorb, Geom g) {
@@ -234,21 +373,28 @@ __global__ void __launch_bounds__(kPT) sphere_cover_kernel(S* __restrict__ st, c
     double c[3];
     load3(A.r, q, c);
     const Cube cube(c, A.half);
+    if (absorb && within_margin(A, q, g)) return;
     const double R2 = __dmul_rn(A.radius, A.radius);
+    const float in2 = absorb && A.radius > 2.0 ? (float)((A.radius - 2.0) * (A.radius - 2.0)) : -1.f;
+    const float Rf = (float)A.radius;
+    float margin = 1e30f;   // distance from the surface of the nearest node
     double acc[6] = {0, 0, 0, 0, 0, 0};
     for (int b = threadIdx.x; b < cube.count(); b += kPT) {
-        int u[3];
-        cube.at(b, g, u);
-        const uint32_t s = site_of(u, g);
-        const double arm[3] = {min_image((double)u[0] - c[0], g.nx), min_image((double)u[1] - c[1], g.ny),
-                               min_image((double)u[2] - c[2], g.nz)};
-        if (norm2(arm[0], arm[1], arm[2]) > R2) continue;
+        int u[3], x[3];
+        cube.at(b, g, u, x);
+        float df[3];
+        const float r2 = cube.dist2(u, df);
+        margin = fminf(margin, fabsf(sqrtf(r2) - Rf));
+        if (r2 < in2) continue;   // covered before the move too
+        if (!covered(cube, u, x, r2, c, R2, g)) continue;
+        const uint32_t s = site_of(x, g);
         if (A.owner[s] == q + 1) continue;   // covered before
         if ((mask && mask[s]) || atomicCAS(A.owner + s, 0, q + 1) != 0) {
             atomicOr(A.err, 1);
             continue;
         }
         if (!absorb) continue;
+        A.moved[q] = 1;
         double m[3] = {0, 0, 0};
         static_for<1, Q>([&](auto I) {
             constexpr int i = decltype(I)::value;
@@ -263,6 +409,8 @@ __global__ void __launch_bounds__(kPT) sphere_cover_kernel(S* __restrict__ st, c
             constexpr int i = decltype(I)::value;
             Store<S>::st2(st + pidx(0, i, s), 0.f, 0.f);
         });
+        const double arm[3] = {disp(x[0], u[0], c[0], g.nx), disp(x[1], u[1], c[1], g.ny),
+                               disp(x[2], u[2], c[2], g.nz)};
         double L[3];
         cross(arm, m, L);
 #pragma unroll
@@ -270,6 +418,20 @@ __global__ void __launch_bounds__(kPT) sphere_cover_kernel(S* __restrict__ st, c
             acc[a] += m[a];
             acc[3 + a] += L[a];
         }
+    }
+    // the margin of this centre (nodes beyond the cube are farther than its
+    // half-width, which exceeds R + 1)
+    __shared__ float mred[kPT];
+    mred[threadIdx.x] = margin;
+    __syncthreads();
+    for (int h = kPT / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) mred[threadIdx.x] = fminf(mred[threadIdx.x], mred[threadIdx.x + h]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        A.margin[q] = fminf(mred[0], 1.0f);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) A.ref[3 * q + a] = c[a];
     }
     if (!absorb) return;
     block_sum(acc);
@@ -282,8 +444,9 @@ __global__ void __launch_bounds__(kPT) sphere_cover_kernel(S* __restrict__ st, c
 }
 
 // Solid flags (bit 0 solid, bit i: x - c_i solid) from the mask and the
-// coverage: over the cube of every sphere widened by one (all sites whose
-// flags a re-meshing can change), or over the whole grid when whole != 0.
+// coverage: over the shell of every sphere's widened cube where a re-meshing
+// can change a flag (within R -/+ 3.5 of the centre), or over the whole
+// grid when whole != 0.
 __global__ void sphere_flags_kernel(uint32_t* __restrict__ flags, const uint8_t* __restrict__ mask, Spheres A,
                                     int whole, Geom g) {
     auto solid = [&](uint32_t s) { return (mask && mask[s]) || A.owner[s] != 0; };
@@ -304,13 +467,19 @@ __global__ void sphere_flags_kernel(uint32_t* __restrict__ flags, const uint8_t*
         return;
     }
     const int q = blockIdx.x;
+    if (!A.moved[q]) return;   // no node changed: neither did a flag
     double c[3];
     load3(A.r, q, c);
     const Cube cube(c, A.half + 1);
+    const float in2 = A.radius > 3.5 ? (float)((A.radius - 3.5) * (A.radius - 3.5)) : -1.f;
+    const float out2 = (float)((A.radius + 3.5) * (A.radius + 3.5));
     for (int b = threadIdx.x; b < cube.count(); b += kPT) {
-        int u[3];
-        cube.at(b, g, u);
-        one(u[0], u[1], u[2]);
+        int u[3], x[3];
+        cube.at(b, g, u, x);
+        float df[3];
+        const float r2 = cube.dist2(u, df);
+        if (r2 < in2 || r2 > out2) continue;
+        one(x[0], x[1], x[2]);
     }
 }
 
@@ -338,8 +507,13 @@ cudaError_t launch_sphere_links(int prec, void* state, const uint32_t* flags, co
 cudaError_t launch_sphere_move(int prec, void* state, uint32_t* flags, const uint8_t* mask, const Spheres& S,
                                const Geom& g, const Phys& p, cudaStream_t st) {
     if (S.n == 0 || !(S.mass > 0.0)) return cudaSuccess;   // fixed spheres never move
+    cudaError_t e = cudaSuccess;
+    if (S.contact_k != 0.0) {   // else the contact forces stay zero
+        sphere_contact_kernel<<<S.n, kCT, 0, st>>>(S, g);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     sphere_update_kernel<<<(S.n + 127) / 128, 128, 0, st>>>(S, g);
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
 #define LBGB_MOVE(T)                                                                  \
     [&] {                                                                             \

@@ -150,10 +150,12 @@ class Solver:
         return {"launches_per_step": v[0].value, "grid_blocks": v[1].value,
                 "block_threads": v[2].value, "z_split": v[3].value}
 
-    def set_particles(self, r, v=None, w=None, radius=5.0, mass=1.0):
+    def set_particles(self, r, v=None, w=None, radius=5.0, mass=1.0, contact=None):
         """Place moving rigid spheres (``lb_particles_set``): centres ``r``,
         velocities ``v`` and angular velocities ``w`` as (n, 3) arrays, one
-        radius and mass (mass <= 0: held fixed). Before ``init``."""
+        radius and mass (mass <= 0: held fixed). Before ``init``.
+        ``contact`` = (stiffness, range) sets the contact force
+        (``lb_particles_contact``)."""
         r = np.ascontiguousarray(np.asarray(r, np.float64).reshape(-1, 3))
         n = len(r)
         arr = lambda a: None if a is None else np.ascontiguousarray(np.asarray(a, np.float64).reshape(n, 3))
@@ -162,6 +164,9 @@ class Solver:
         _lib.check(_lib.lib().lb_particles_set(self._h, n, ptr(r), ptr(v), ptr(w), float(radius), float(mass)),
                    "lb_particles_set")
         self.n_particles = n
+        if contact is not None:
+            _lib.check(_lib.lib().lb_particles_contact(self._h, float(contact[0]), float(contact[1])),
+                       "lb_particles_contact")
 
     def particles(self):
         """The spheres after the last step: dict of (n, 3) arrays r, v, w and

@@ -187,3 +187,30 @@ def test_full_size_256_tiled_moving_spheres():
     q = s.particles()
     assert np.abs(q["r"] - np.mod(parts.r[0] + offs, n)).max() <= 1e-5
     assert np.abs(q["F"] - parts.F[0]).max() <= 4e-6 * np.abs(parts.F).max()
+
+
+def test_contact_force_turns_spheres_back_as_the_oracle():
+    """Two spheres sent at each other through fluid at rest, turned back by
+    the contact force: positions and velocities follow the oracle's."""
+    shape = (32, 16, 16)
+    nx, ny, nz = shape
+    rho0 = (0.5, 0.5)
+    sph = dict(r=[[11.3, 8.0, 8.0], [20.7, 8.0, 8.0]], v=[[0.06, 0, 0], [-0.06, 0, 0]], radius=3.5, mass=1000.0)
+    rA = np.full((nz, ny, nx), 0.5)
+    rB = np.full((nz, ny, nx), 0.5)
+    u = np.zeros((3, nz, ny, nx))
+    s = Solver(nx, ny, nz, 1.0, 0.0, max_particles=2, rho0=rho0)
+    s.set_particles(sph["r"], sph["v"], None, sph["radius"], sph["mass"], contact=(0.5, 1.5))
+    s.init(dev(rA), dev(rB), dev(u))
+    parts = op.Particles(sph["r"], sph["v"], None, sph["radius"], sph["mass"], contact=(0.5, 1.5))
+    owner = op.coverage((nz, ny, nx), parts.r, parts.radius)
+    g = op.init(rA, rB, u, None, owner)
+    turned = False
+    for _ in range(70):
+        s.step(1)
+        g, owner = op.step(g, owner, None, parts, 1.0, 0.0, rho0)
+        p = s.particles()
+        assert np.abs(p["r"] - parts.r).max() <= 1e-5
+        assert np.abs(p["v"] - parts.v).max() <= 1e-5 * 0.06       # of the initial speed
+        turned = turned or parts.v[0][0] < 0
+    assert turned and p["v"][0][0] < 0
