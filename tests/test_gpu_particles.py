@@ -214,3 +214,30 @@ def test_contact_force_turns_spheres_back_as_the_oracle():
         assert np.abs(p["v"] - parts.v).max() <= 1e-5 * 0.06       # of the initial speed
         turned = turned or parts.v[0][0] < 0
     assert turned and p["v"][0][0] < 0
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_moving_spheres_between_static_walls(prec):
+    """Spheres and a static mask together: two solid planes (a channel in y)
+    bounce back at rest through the mask's link lists, the spheres through
+    their own links; the state and the spheres follow the oracle."""
+    shape = (32, 28, 24)
+    nx, ny, nz = shape
+    mask = np.zeros((nz, ny, nx), np.uint8)
+    mask[:, 0, :] = 1
+    mask[:, ny - 1, :] = 1
+    sph = dict(r=[[9.3, 10.4, 7.7], [23.6, 17.2, 15.9]], v=[[0.21, 0.05, 0.07], [-0.15, -0.04, 0.18]],
+               w=[[0.0, 0.01, -0.02], [0.015, 0.0, 0.01]], radius=3.2, mass=60.0)
+    rA, rB, u = fields(shape, 6)
+    s = gpu_run(shape, sph, 0, 0.9, 0.6, rA, rB, u, prec=prec, mask=mask)
+    g, owner, parts, rho0 = oracle_init(shape, sph, rA, rB, u, mask)
+    for _ in range(6):
+        s.step(1)
+        g, owner = op.step(g, owner, mask, parts, 0.9, 0.6, rho0)
+    p = s.particles()
+    bars = BARS[prec]
+    assert np.abs(p["r"] - parts.r).max() <= bars["r"]
+    assert np.abs(p["v"] - parts.v).max() <= bars["v"] * np.abs(parts.v).max()
+    got = s.get_state().cpu().numpy().astype(np.float64)
+    want = ln.to_public(op.pulled(g, owner, mask, parts, rho0))
+    assert np.abs(got - want).max() <= bars["state"] * np.abs(want).max()
