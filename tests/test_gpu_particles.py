@@ -290,3 +290,30 @@ def test_moving_sphere_drag_equals_fixed_sphere_in_uniform_flow():
         late[mode] = np.mean(F)
     assert late["fixed"] < 0 and late["moving"] < 0
     assert abs(late["moving"] / late["fixed"] - 1.0) < 0.03
+
+
+def test_collision_with_the_mask_and_overspeed_are_reported():
+    """Failure detection on the host: a sphere driven into a solid wall of
+    the mask, or one moving faster than a node per step, leaves the run
+    invalid, which lb_particles_get reports as LB_ESTATE (the arrays are
+    still filled); no device fault is involved."""
+    shape = (32, 24, 20)
+    nx, ny, nz = shape
+    rA, rB, u = fields(shape, 7)
+    mask = np.zeros((nz, ny, nx), np.uint8)
+    mask[:, :, 25:] = 1                                          # a wall at x >= 25
+    s = Solver(nx, ny, nz, 1.0, 0.5, mask=mask, max_particles=1)
+    # slow enough that every population stays positive (bias 0.017 < w rho0 = 0.028)
+    s.set_particles([[20.0, 12.0, 10.0]], v=[[0.1, 0.0, 0.0]], radius=3.0, mass=1e9)
+    s.init(dev(rA), dev(rB), dev(u))
+    s.step(35)                                                   # reaches the wall after ~20 steps
+    with pytest.raises(_lib.LbError) as e:
+        s.particles()
+    assert e.value.status == _lib.LB_ESTATE
+    f = Solver(nx, ny, nz, 1.0, 0.5, max_particles=1)
+    f.set_particles([[10.0, 12.0, 10.0]], v=[[1.5, 0.0, 0.0]], radius=3.0, mass=1e9)
+    f.init(dev(rA), dev(rB), dev(u))
+    f.step(1)
+    with pytest.raises(_lib.LbError) as e:
+        f.particles()
+    assert e.value.status == _lib.LB_ESTATE
