@@ -74,6 +74,20 @@ def test_workspace_bytes(L):
     assert _lib.workspace_bytes(8, 8, 8, _lib.options(ckpt_every=4, ckpt_steps_max=0)) == 0
 
 
+def test_sphere_options_and_workspace(L):
+    """Room for moving spheres: an owner word per site plus per-sphere state;
+    spheres need the Shan-Chen model, the fused kernel and no recording."""
+    n = 32 ** 3
+    wb = _lib.workspace_bytes(32, 32, 32, _lib.options())
+    wp = _lib.workspace_bytes(32, 32, 32, _lib.options(max_particles=100))
+    assert wp >= wb + n * 4 + 100 * 15 * 8
+    assert _lib.workspace_bytes(32, 32, 32, _lib.options(max_particles=-1)) == 0
+    assert _lib.workspace_bytes(32, 32, 32, _lib.options(kernel="two_pass", max_particles=4)) == 0
+    assert _lib.workspace_bytes(32, 32, 32, _lib.options(ckpt_every=4, ckpt_steps_max=8, max_particles=4)) == 0
+    cg = dict(nu=(1 / 6, 1 / 6), sigma=0.01, beta=0.7)
+    assert _lib.workspace_bytes(32, 32, 32, _lib.options(model="colour_gradient", cg=cg, max_particles=4)) == 0
+
+
 @pytest.mark.parametrize("args", [
     dict(nx=2, ny=8, nz=8, tau=1.0, G=0.5),
     dict(nx=8, ny=8, nz=8, tau=0.5, G=0.5),
