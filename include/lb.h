@@ -204,8 +204,10 @@ lb_status lb_launch_info(const lb_ctx* ctx, int* launches_per_step, int* grid_bl
  *   radius       > 0; 2 (ceil(radius) + 3) + 1 <= min(nx, ny, nz).
  *   mass         > 0, or <= 0 for spheres held fixed (forces still computed).
  * Call after lb_create and before lb_init (LB_ESTATE otherwise). LB_EINVAL
- * for bad values, spheres closer than 2 radius (periodic) or covering a
- * solid node of the mask. Synchronous. */
+ * for bad values, spheres closer than 2 radius (periodic; checked on the host
+ * with a cell list) or covering a solid node of the mask. Synchronous. The
+ * contact force (lb_particles_contact) visits every pair of spheres each
+ * step: meant for up to about 10^4 spheres. */
 lb_status lb_particles_set(lb_ctx* ctx, int n, const double* r, const double* v, const double* w, double radius,
                            double mass);
 

@@ -518,17 +518,60 @@ lb_status lb_particles_set(lb_ctx* c, int n, const double* r, const double* v, c
             h[3 * (size_t)n + 3 * q + a] = vv;
             h[6 * (size_t)n + 3 * q + a] = ww;
         }
-    // spheres closer than two radii (periodic) would share nodes
-    for (int p = 0; p < n; ++p)
-        for (int q = p + 1; q < n; ++q) {
-            double d2 = 0.0;
-            for (int a = 0; a < 3; ++a) {
-                double d = h[3 * p + a] - h[3 * q + a];
-                d -= dims[a] * std::nearbyint(d / dims[a]);
-                d2 += d * d;
-            }
-            if (d2 <= 4.0 * radius * radius) return LB_EINVAL;
+    // spheres closer than two radii (periodic) would share nodes: checked over
+    // cells at least two radii wide (at most about 4n of them), each sphere
+    // against the spheres of the up to 27 distinct cells around its own
+    if (n > 1) {
+        int nc[3];
+        long long cells = 1;
+        for (int a = 0; a < 3; ++a) {
+            nc[a] = std::max(1, (int)std::floor(dims[a] / (2.0 * radius)));
+            cells *= nc[a];
         }
+        while (cells > 4LL * n + 64) {   // coarser cells: fewer of them, more pairs each
+            const int a = nc[0] >= nc[1] && nc[0] >= nc[2] ? 0 : (nc[1] >= nc[2] ? 1 : 2);
+            cells = cells / nc[a] * ((nc[a] + 1) / 2);
+            nc[a] = (nc[a] + 1) / 2;
+        }
+        auto cell_of = [&](int q, int (&ci)[3]) {
+            for (int a = 0; a < 3; ++a) ci[a] = std::min(nc[a] - 1, (int)(h[3 * q + a] * nc[a] / dims[a]));
+        };
+        std::vector<int> key(n), order(n);
+        for (int q = 0; q < n; ++q) {
+            int ci[3];
+            cell_of(q, ci);
+            key[q] = ci[0] + nc[0] * (ci[1] + nc[1] * ci[2]);
+            order[q] = q;
+        }
+        std::sort(order.begin(), order.end(), [&](int a, int b) { return key[a] < key[b]; });
+        std::vector<int> start((size_t)cells + 1, 0);
+        for (int q = 0; q < n; ++q) ++start[(size_t)key[q] + 1];
+        for (long long k = 0; k < cells; ++k) start[(size_t)k + 1] += start[(size_t)k];
+        for (int p = 0; p < n; ++p) {
+            int ci[3];
+            cell_of(p, ci);
+            int near[27], m = 0;
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const int k = (ci[0] + dx + nc[0]) % nc[0] +
+                                      nc[0] * ((ci[1] + dy + nc[1]) % nc[1] + nc[1] * ((ci[2] + dz + nc[2]) % nc[2]));
+                        if (std::find(near, near + m, k) == near + m) near[m++] = k;
+                    }
+            for (int j = 0; j < m; ++j)
+                for (int t = start[(size_t)near[j]]; t < start[(size_t)near[j] + 1]; ++t) {
+                    const int q = order[t];
+                    if (q <= p) continue;
+                    double d2 = 0.0;
+                    for (int a = 0; a < 3; ++a) {
+                        double d = h[3 * p + a] - h[3 * q + a];
+                        d -= dims[a] * std::nearbyint(d / dims[a]);
+                        d2 += d * d;
+                    }
+                    if (d2 <= 4.0 * radius * radius) return LB_EINVAL;
+                }
+        }
+    }
     Spheres& S = c->sph;
     const size_t P3 = (size_t)c->opt.max_particles * 3;
     cudaError_t e = cudaSuccess;
