@@ -332,9 +332,10 @@ def main_particles(args, W, world, rank, local):
                    "launch": info},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": peak_kind, "algorithmic_bytes_per_site": alg_bytes,
-                     "timed": "the whole step (%d launches: sphere links, step kernel, leap-frog, two re-meshing "
-                              "passes, flags)" % info["launches_per_step"],
-                     "traffic": None},
+                     "timed": "the whole step (%d launches: sphere links, step kernel, contact, leap-frog, two "
+                              "re-meshing passes, flags)" % info["launches_per_step"],
+                     "traffic": (lambda t: t * N if t is not None and (nx, ny, nz) == (256, 256, 256) else None)(
+                         traffic_per_site("particles_" + args.prec))},
         "gpu_launches": args.steps * info["launches_per_step"],
         "fluid_glups": glups * fluid,
         "clocks": clocks,
