@@ -172,3 +172,14 @@ def test_contact_force_conserves_momentum_and_parts_spheres():
         turned = turned or parts.v[0][0] < 0
         touched = touched or np.abs(parts.Fc).max() > 0
     assert turned and touched
+
+
+def test_coverage_matches_the_input_generators_masks():
+    """The sphere coverage rule (periodic distance <= R) is the one the seeded
+    colloid masks use, so a mask made from the same centres marks the same
+    nodes (the benchmark takes its fluid fraction from such a mask)."""
+    from paper_2112_08264_gb300 import inputs
+    nx, ny, nz, R = 40, 36, 28, 5.5
+    mask, centres = inputs.colloid_mask(nx, ny, nz, n_spheres=12, radius=R, seed=3)
+    owner = op.coverage((nz, ny, nx), centres, R)
+    assert np.array_equal(owner >= 0, mask == 1)
