@@ -66,7 +66,9 @@ cudaError_t launch_step(const StepLaunch& L, cudaStream_t st);
 void fused_geometry(int nx, int ny, int nz, int sm_count, int* tiles, int* zsplit, int* threads);
 
 // Async fused kernel: plan for a grid, and its launcher (called by launch_step).
-AsyncPlan plan_fused_async(int nx, int ny, int nz, int sm_count, int prec, bool masked, size_t smem_limit);
+// model: 0 Shan-Chen, 1 colour gradient (the 16-bit tiling depends on it).
+AsyncPlan plan_fused_async(int nx, int ny, int nz, int sm_count, int prec, bool masked, int model,
+                           size_t smem_limit);
 cudaError_t launch_fused_async(const StepLaunch& L, cudaStream_t st);
 
 // Solid flags from a device mask (1 = solid).

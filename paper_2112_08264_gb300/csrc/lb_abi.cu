@@ -261,7 +261,7 @@ lb_status lb_create(int nx, int ny, int nz, float tau, float G, const uint8_t* m
     c->sm_count = sms;
     fused_geometry(nx, ny, nz, sms, &c->tiles, &c->zsplit, &c->threads);
     // spheres make solid nodes too: the masked kernel (flag boxes in shared memory) steps them
-    c->plan = plan_fused_async(nx, ny, nz, sms, o.prec, mask != nullptr || o.max_particles > 0,
+    c->plan = plan_fused_async(nx, ny, nz, sms, o.prec, mask != nullptr || o.max_particles > 0, o.model,
                                (size_t)smem_optin);
     if ((o.kernel == LB_KERNEL_FUSED && c->plan.nst < 2) || (c->particles && !c->plan.box)) {
         // no tile fits in shared memory, or spheres on a grid the box kernel cannot step

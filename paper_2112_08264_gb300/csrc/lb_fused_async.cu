@@ -569,6 +569,9 @@ cudaError_t launch_box_t(const StepLaunch& L, cudaStream_t st) {
     if (configured < P.smem) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem);
         if (e != cudaSuccess) return e;
+        // room for two resident blocks where the plan wants them
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        if (e != cudaSuccess) return e;
         configured = P.smem;
     }
     dim3 grid(P.ncols * P.R, P.zsplit, 1);
@@ -622,7 +625,8 @@ cudaError_t launch_fused_async(const StepLaunch& L, cudaStream_t st) {
     }
 }
 
-AsyncPlan plan_fused_async(int nx, int ny, int nz, int sm_count, int prec, bool masked, size_t smem_limit) {
+AsyncPlan plan_fused_async(int nx, int ny, int nz, int sm_count, int prec, bool masked, int model,
+                           size_t smem_limit) {
     AsyncPlan best{};
     double best_cost = 1e300;
     const int ncols = (nx + kTX - 1) / kTX;
@@ -671,6 +675,37 @@ AsyncPlan plan_fused_async(int nx, int ny, int nz, int sm_count, int prec, bool 
                 best.box = box ? 1 : 0;
             }
             if (blocks >= sm_count) break;   // more z-splits only add halo planes
+        }
+    }
+    // 16-bit storage on masked grids and for the colour gradient (the
+    // heavier per-node work): where short tiles fill exactly one wave of two
+    // resident blocks per SM (half of the SM's shared memory each), take them
+    // instead, so that the two blocks' barriers interleave. Measured at 256^3:
+    // colour gradient FP16 +19 %, masked FP16 +1.4 %; unmasked Shan-Chen
+    // FP16 -0.2 % and FP32 -3 % (those keep one block of tall tiles).
+    if (esize == 2 && box && best.zsplit == 1 && (masked || model == 1)) {
+        const size_t half_limit = (smem_limit + 1024) / 2 - 1024;
+        for (int R = best.R + 1; R <= ny && (long long)ncols * R <= 2LL * sm_count; ++R) {
+            if ((long long)ncols * R != 2LL * sm_count) continue;
+            const int tymax = (ny + R - 1) / R;
+            const int threads = kTX * tymax;
+            const int ns = threads + 2 * (kTX + 2) + 2 * tymax;
+            if (threads < 2 * (kTX + 2) + 2 * tymax || threads < (tymax + 2) * cpr) continue;
+            const size_t stage = (size_t)(tymax + 2) * row_bytes + (masked ? (size_t)(tymax + 2) * 40 * 4 : 0);
+            const size_t ring = (size_t)4 * (tymax + 2) * (kTX + 2) * 8;
+            const size_t lists = masked ? ((size_t)(nz + 1) * 4 + 15) / 16 * 16 : 0;
+            if (half_limit < ring + lists + 3 * stage) continue;
+            int nst = (int)((half_limit - ring - lists) / stage);
+            nst = nst > 4 ? 4 : nst;
+            best.R = R;
+            best.tymax = tymax;
+            best.zsplit = 1;
+            best.zchunk = nz;
+            best.nst = nst;
+            best.threads = threads;
+            best.ns = ns;
+            best.smem = ring + lists + (size_t)nst * stage;
+            break;
         }
     }
     return best;
