@@ -24,7 +24,11 @@ no populations. Per step, in this order:
    repulsive contact force that keeps spheres apart (the paper names a
    Hertzian one): between two spheres whose centres are d < 2 R + delta
    apart, k (2 R + delta - d)^(3/2) along the line of centres, pushing them
-   apart (k = 0: none).
+   apart (k = 0: none). With a lubrication cutoff h_c > 0, two spheres whose
+   gap h = d - 2R is below h_c also exchange the normal lubrication force
+   -(3/2) pi mu R^2 (1/h - 1/h_c) ((v_i - v_j) . n) n (mu = (rho0^A + rho0^B)
+   (tau - 1/2) / 3, n the unit vector from j to i, h clamped at 0.01 from
+   below), from the velocities before the update.
 4. Re-meshing: nodes the moved sphere no longer covers become fluid with the
    equilibrium populations of density rho0^k and the local wall velocity;
    nodes it newly covers lose their fluid. The particle takes up the
@@ -40,7 +44,9 @@ Readings where the paper is silent (listed with the design notes):
 * the re-meshing rule (item 4) is not given in the paper; it is chosen to
   conserve momentum exactly;
 * the contact force's law and constants are not given; the Hertzian form
-  above with stiffness k and range delta is the reading.
+  above with stiffness k and range delta is the reading;
+* the lubrication force is named with its range (2/3 of a lattice unit)
+  but not given: the normal lubrication correction above is the reading.
 
 State (the library's write-side representation): g holds the post-collision
 populations at fluid nodes and, at solid nodes, the slots the next pull
@@ -96,7 +102,7 @@ class Particles:
     """Rigid spheres: positions r, velocities v, angular velocities w (all
     (P, 3) float64), a common radius and mass (mass <= 0: fixed)."""
 
-    def __init__(self, r, v=None, w=None, radius=5.0, mass=1.0, contact=(0.0, 0.0)):
+    def __init__(self, r, v=None, w=None, radius=5.0, mass=1.0, contact=(0.0, 0.0), lubrication=0.0):
         self.r = np.array(r, dtype=np.float64).reshape(-1, 3)
         P = len(self.r)
         self.v = np.zeros((P, 3)) if v is None else np.array(v, dtype=np.float64).reshape(P, 3)
@@ -107,13 +113,14 @@ class Particles:
         self.T = np.zeros((P, 3))
         self.Fc = np.zeros((P, 3))
         self.contact = (float(contact[0]), float(contact[1]))
+        self.lubrication = float(lubrication)
 
     @property
     def inertia(self):
         return 0.4 * self.mass * self.radius ** 2
 
     def copy(self):
-        c = Particles(self.r, self.v, self.w, self.radius, self.mass, self.contact)
+        c = Particles(self.r, self.v, self.w, self.radius, self.mass, self.contact, self.lubrication)
         c.F, c.T, c.Fc = self.F.copy(), self.T.copy(), self.Fc.copy()
         return c
 
@@ -224,30 +231,40 @@ def collide(f, tau, G, gbody, solid):
     return out
 
 
-def contact_forces(parts, box):
-    """Repulsive pair forces k (2 R + delta - d)^(3/2) along the line of
-    centres for centre distances d < 2 R + delta (minimum image)."""
+def contact_forces(parts, box, mu=0.0):
+    """Pair forces: the repulsion k (2 R + delta - d)^(3/2) along the line of
+    centres for centre distances d < 2 R + delta, and the normal lubrication
+    force for gaps below the cutoff (minimum image; mu the dynamic
+    viscosity)."""
     k, delta = parts.contact
+    hc = parts.lubrication
     P = len(parts.r)
     Fc = np.zeros((P, 3))
-    if k == 0.0:
+    if k == 0.0 and hc == 0.0:
         return Fc
-    reach = 2.0 * parts.radius + delta
+    R = parts.radius
+    reach = 2.0 * R + delta
     for i in range(P):
         for j in range(P):
             if i == j:
                 continue
             d = np.array([min_image(parts.r[i][a] - parts.r[j][a], box[a]) for a in range(3)])
             dist = np.sqrt((d * d).sum())
-            if dist < reach:
-                Fc[i] += k * (reach - dist) ** 1.5 * d / dist
+            n = d / dist
+            if k != 0.0 and dist < reach:
+                Fc[i] += k * (reach - dist) ** 1.5 * n
+            h = dist - 2.0 * R
+            if hc > 0.0 and h < hc:
+                h = max(h, 0.01)
+                vn = ((parts.v[i] - parts.v[j]) * n).sum()
+                Fc[i] -= 1.5 * np.pi * mu * R * R * (1.0 / h - 1.0 / hc) * vn * n
     return Fc
 
 
-def advance(parts, box):
-    """Step 3: leap-frog with the force and torque of step 1 and the contact
-    forces of the current places (box = (nx, ny, nz))."""
-    parts.Fc = contact_forces(parts, box)
+def advance(parts, box, mu=0.0):
+    """Step 3: leap-frog with the force and torque of step 1 and the pair
+    forces of the current places and velocities (box = (nx, ny, nz))."""
+    parts.Fc = contact_forces(parts, box, mu)
     if parts.mass <= 0:
         return
     parts.v = parts.v + (parts.F + parts.Fc) / parts.mass
@@ -309,7 +326,7 @@ def step(g, owner, mask, parts, tau, G, rho0, gbody=None):
     solid = _solid(mask, owner)
     gnew = collide(post_streaming(g), tau, G, gbody, solid)
     nz, ny, nx = g.shape[2:]
-    advance(parts, (nx, ny, nz))
+    advance(parts, (nx, ny, nz), (rho0[0] + rho0[1]) * (tau - 0.5) / 3.0)
     gnew, owner = remesh(gnew, owner, mask, parts, rho0)
     return gnew, owner
 

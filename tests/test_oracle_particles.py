@@ -183,3 +183,33 @@ def test_coverage_matches_the_input_generators_masks():
     mask, centres = inputs.colloid_mask(nx, ny, nz, n_spheres=12, radius=R, seed=3)
     owner = op.coverage((nz, ny, nx), centres, R)
     assert np.array_equal(owner >= 0, mask == 1)
+
+
+def test_lubrication_damps_the_approach_and_conserves_momentum():
+    """Two spheres closing at a gap inside the lubrication range: the normal
+    lubrication force is a pair force (total momentum conserved), it opposes
+    the relative normal velocity, so the approach is slower than without it."""
+    shape = (16, 16, 32)
+    rho0 = (0.5, 0.5)
+
+    def run(hc):
+        parts = op.Particles([[12.6, 8.0, 8.0], [19.4, 8.0, 8.0]], v=[[0.004, 0, 0], [-0.004, 0, 0]], radius=3.2,
+                             mass=2000.0, lubrication=hc)
+        owner = op.coverage(shape, parts.r, parts.radius)
+        g = np.stack([ln.equilibrium(np.full(shape, rho0[k]), np.zeros((3,) + shape)) for k in range(2)])
+        g = g * (owner < 0)
+        p0 = op.fluid_momentum(g, owner, None) + parts.mass * parts.v.sum(axis=0)
+        M = op.fluid_mass(g, owner, None)
+        work = 0.0
+        for _ in range(8):
+            g, owner = op.step(g, owner, None, parts, 1.0, 0.0, rho0)
+            p1 = op.fluid_momentum(g, owner, None) + parts.mass * parts.v.sum(axis=0)
+            assert np.abs(p1 - p0).max() <= 1e-14 * M
+            work += (parts.Fc[0] * (parts.v[0] - parts.v[1])).sum()
+        return parts.v[0][0] - parts.v[1][0], work, np.abs(parts.Fc).max()
+
+    rel_free, _, f_free = run(0.0)
+    rel_lub, work, f_lub = run(2.0 / 3.0)
+    assert f_free == 0.0 and f_lub > 0.0
+    assert work < 0.0                        # the force opposes the relative motion
+    assert 0.0 < rel_lub < rel_free          # still closing, more slowly
