@@ -220,6 +220,17 @@ lb_status lb_particles_set(lb_ctx* ctx, int n, const double* r, const double* v,
  * LB_ESTATE without room for spheres. Host function. */
 lb_status lb_particles_contact(lb_ctx* ctx, double stiffness, double range);
 
+/* Lubrication between spheres (the paper adds one for particles closer than
+ * 2/3 of a lattice unit; its form is not given): two spheres whose gap
+ * h = d - 2 radius is below cutoff exchange the normal lubrication force
+ * -(3/2) pi mu radius^2 (1/h - 1/cutoff) ((v_i - v_j) . n) n, n the unit
+ * vector between the centres, mu = (rho0^A + rho0^B) (tau - 1/2) / 3, h
+ * clamped at 0.01, from the velocities before the leap-frog update; added to
+ * the contact force. cutoff = 0 (the default) turns it off. Any time after
+ * lb_create; LB_EINVAL for a negative or non-finite cutoff, LB_ESTATE without
+ * room for spheres. Host function. */
+lb_status lb_particles_lubrication(lb_ctx* ctx, double cutoff);
+
 /* The spheres after the last step, into HOST arrays of 3n doubles (any may
  * be NULL): r, v, w as above, and F, T = the force and torque of the last
  * step's links. LB_ESTATE (arrays still filled) when a step met spheres that

@@ -80,6 +80,7 @@ def lib():
     L.lb_particles_set.argtypes = [_VP, ctypes.c_int, _DP, _DP, _DP, ctypes.c_double, ctypes.c_double]
     L.lb_particles_get.argtypes = [_VP, _DP, _DP, _DP, _DP, _DP]
     L.lb_particles_contact.argtypes = [_VP, ctypes.c_double, ctypes.c_double]
+    L.lb_particles_lubrication.argtypes = [_VP, ctypes.c_double]
     L.lb_link_info.argtypes = [_VP, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                                ctypes.POINTER(ctypes.c_int)]
     L.lb_moments_noalloc.argtypes = ([ctypes.c_int] * 3 + [ctypes.c_float, ctypes.POINTER(ctypes.c_double),
@@ -93,7 +94,8 @@ def lib():
     L.lb_last_error.restype = ctypes.c_char_p
     for name in ("lb_create", "lb_set_stream", "lb_init", "lb_step", "lb_moments", "lb_stats",
                  "lb_get_state", "lb_set_state", "lb_backward", "lb_launch_info", "lb_link_info",
-                 "lb_particles_set", "lb_particles_get", "lb_particles_contact"):
+                 "lb_particles_set", "lb_particles_get", "lb_particles_contact",
+                 "lb_particles_lubrication"):
         getattr(L, name).restype = ctypes.c_int
     # one-component BGK (include/lb1.h)
     L.lb1_workspace_bytes.argtypes = [ctypes.c_int] * 4

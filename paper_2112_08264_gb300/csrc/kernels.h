@@ -117,6 +117,8 @@ struct Spheres {
     int n = 0;
     double radius = 0.0, mass = 0.0, inertia = 0.0;
     double contact_k = 0.0, contact_range = 0.0;   // k (2R + range - d)^(3/2) for d < 2R + range
+    double lub_cut = 0.0;   // lubrication below this gap (0: none)
+    double mu = 0.0;        // dynamic viscosity for the lubrication force
     int half = 0;   // box half-width around a centre: ceil(radius) + 2
 };
 // Moving-wall bounce-back into the solid slots of `state` and, when

@@ -488,7 +488,7 @@ lb_status lb_launch_info(const lb_ctx* c, int* launches, int* blocks, int* threa
     // spheres: their links, and when they move the update, two re-meshing passes and the flags
     const int sph = !c->particles || c->sph.n == 0
                         ? 0
-                        : (c->sph.mass > 0.0 ? 5 + (c->sph.contact_k != 0.0 ? 1 : 0) : 1);
+                        : (c->sph.mass > 0.0 ? 5 + (c->sph.contact_k != 0.0 || c->sph.lub_cut > 0.0 ? 1 : 0) : 1);
     if (launches) *launches = (k == LB_KERNEL_TWO_PASS ? 2 : 1) + reflect_launches(c) + sph;
     if (blocks)
         *blocks = k == LB_KERNEL_FUSED ? c->plan.ncols * c->plan.R * c->plan.zsplit
@@ -609,6 +609,14 @@ lb_status lb_particles_contact(lb_ctx* c, double stiffness, double range) {
     if (!std::isfinite(stiffness) || stiffness < 0.0 || !std::isfinite(range) || range < 0.0) return LB_EINVAL;
     c->sph.contact_k = stiffness;
     c->sph.contact_range = range;
+    return LB_OK;
+}
+
+lb_status lb_particles_lubrication(lb_ctx* c, double cutoff) {
+    if (!c) return LB_EINVAL;
+    if (!c->particles) return LB_ESTATE;
+    if (!std::isfinite(cutoff) || cutoff < 0.0) return LB_EINVAL;
+    c->sph.lub_cut = cutoff;
     return LB_OK;
 }
 

@@ -239,16 +239,21 @@ __global__ void __launch_bounds__(kPT) sphere_links_kernel(S* __restrict__ st, c
     }
 }
 
-// Contact forces: k (2R + range - d)^(3/2) along the line of centres for
-// every other sphere whose centre is d < 2R + range away (minimum image),
-// pushing the two apart. One block per sphere, partners split over its
-// threads in index order; an FP32 distance test skips the far ones.
+// Pair forces: the contact repulsion k (2R + range - d)^(3/2) along the line
+// of centres for every other sphere whose centre is d < 2R + range away
+// (minimum image), and the normal lubrication force
+// -(3/2) pi mu R^2 (1/h - 1/h_c) ((v_i - v_j) . n) n for gaps h = d - 2R
+// below h_c (h clamped at 0.01), from the velocities before the update. One
+// block per sphere, partners split over its threads in index order; an FP32
+// distance test skips the far ones.
 constexpr int kCT = 128;
 __global__ void __launch_bounds__(kCT) sphere_contact_kernel(Spheres A, Geom g) {
     const int q = blockIdx.x;
     const int n[3] = {g.nx, g.ny, g.nz};
     const double reach = 2.0 * A.radius + A.contact_range;
-    const float near2 = (float)((reach + 0.5) * (reach + 0.5));
+    const double far = fmax(reach, 2.0 * A.radius + A.lub_cut);
+    const float near2 = (float)((far + 0.5) * (far + 0.5));
+    const double lub = 1.5 * 3.14159265358979323846 * A.mu * A.radius * A.radius;
     double c[3];
     float cf[3];
     load3(A.r, q, c);
@@ -268,8 +273,16 @@ __global__ void __launch_bounds__(kCT) sphere_contact_kernel(Spheres A, Geom g) 
 #pragma unroll
         for (int a = 0; a < 3; ++a) d[a] = min_image(c[a] - A.r[3 * j + a], n[a]);
         const double dist = sqrt(norm2(d[0], d[1], d[2]));
-        if (!(dist < reach)) continue;
-        const double f = A.contact_k * pow(reach - dist, 1.5);
+        double f = 0.0;   // along n = d / dist
+        if (A.contact_k != 0.0 && dist < reach) f += A.contact_k * pow(reach - dist, 1.5);
+        const double h = dist - 2.0 * A.radius;
+        if (A.lub_cut > 0.0 && h < A.lub_cut) {
+            double vn = 0.0;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) vn += (A.v[3 * q + a] - A.v[3 * j + a]) * d[a] / dist;
+            f -= lub * (1.0 / fmax(h, 0.01) - 1.0 / A.lub_cut) * vn;
+        }
+        if (f == 0.0) continue;
 #pragma unroll
         for (int a = 0; a < 3; ++a) F[a] += f * d[a] / dist;
     }
@@ -508,8 +521,10 @@ cudaError_t launch_sphere_move(int prec, void* state, uint32_t* flags, const uin
                                const Geom& g, const Phys& p, cudaStream_t st) {
     if (S.n == 0 || !(S.mass > 0.0)) return cudaSuccess;   // fixed spheres never move
     cudaError_t e = cudaSuccess;
-    if (S.contact_k != 0.0) {   // else the contact forces stay zero
-        sphere_contact_kernel<<<S.n, kCT, 0, st>>>(S, g);
+    if (S.contact_k != 0.0 || S.lub_cut > 0.0) {   // else the pair forces stay zero
+        Spheres T = S;
+        T.mu = ((double)p.rho0[0] + (double)p.rho0[1]) * ((double)p.tau - 0.5) / 3.0;
+        sphere_contact_kernel<<<S.n, kCT, 0, st>>>(T, g);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     sphere_update_kernel<<<(S.n + 127) / 128, 128, 0, st>>>(S, g);

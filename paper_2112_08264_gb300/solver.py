@@ -150,12 +150,13 @@ class Solver:
         return {"launches_per_step": v[0].value, "grid_blocks": v[1].value,
                 "block_threads": v[2].value, "z_split": v[3].value}
 
-    def set_particles(self, r, v=None, w=None, radius=5.0, mass=1.0, contact=None):
+    def set_particles(self, r, v=None, w=None, radius=5.0, mass=1.0, contact=None, lubrication=None):
         """Place moving rigid spheres (``lb_particles_set``): centres ``r``,
         velocities ``v`` and angular velocities ``w`` as (n, 3) arrays, one
         radius and mass (mass <= 0: held fixed). Before ``init``.
         ``contact`` = (stiffness, range) sets the contact force
-        (``lb_particles_contact``)."""
+        (``lb_particles_contact``), ``lubrication`` = the gap below which the
+        lubrication force acts (``lb_particles_lubrication``)."""
         r = np.ascontiguousarray(np.asarray(r, np.float64).reshape(-1, 3))
         n = len(r)
         arr = lambda a: None if a is None else np.ascontiguousarray(np.asarray(a, np.float64).reshape(n, 3))
@@ -167,6 +168,8 @@ class Solver:
         if contact is not None:
             _lib.check(_lib.lib().lb_particles_contact(self._h, float(contact[0]), float(contact[1])),
                        "lb_particles_contact")
+        if lubrication is not None:
+            _lib.check(_lib.lib().lb_particles_lubrication(self._h, float(lubrication)), "lb_particles_lubrication")
 
     def particles(self):
         """The spheres after the last step: dict of (n, 3) arrays r, v, w and

@@ -317,3 +317,29 @@ def test_collision_with_the_mask_and_overspeed_are_reported():
     with pytest.raises(_lib.LbError) as e:
         f.particles()
     assert e.value.status == _lib.LB_ESTATE
+
+
+def test_lubrication_as_the_oracle():
+    """Two spheres closing inside the lubrication range: positions and
+    velocities follow the oracle's (the normal lubrication force from the
+    velocities before each update)."""
+    shape = (32, 16, 16)
+    nx, ny, nz = shape
+    rho0 = (0.5, 0.5)
+    sph = dict(r=[[12.6, 8.0, 8.0], [19.4, 8.0, 8.0]], v=[[0.004, 0, 0], [-0.004, 0, 0]], radius=3.2, mass=2000.0)
+    rA = np.full((nz, ny, nx), 0.5)
+    rB = np.full((nz, ny, nx), 0.5)
+    u = np.zeros((3, nz, ny, nx))
+    s = Solver(nx, ny, nz, 1.0, 0.0, max_particles=2, rho0=rho0)
+    s.set_particles(sph["r"], sph["v"], None, sph["radius"], sph["mass"], lubrication=2.0 / 3.0)
+    s.init(dev(rA), dev(rB), dev(u))
+    parts = op.Particles(sph["r"], sph["v"], None, sph["radius"], sph["mass"], lubrication=2.0 / 3.0)
+    owner = op.coverage((nz, ny, nx), parts.r, parts.radius)
+    g = op.init(rA, rB, u, None, owner)
+    for _ in range(8):
+        s.step(1)
+        g, owner = op.step(g, owner, None, parts, 1.0, 0.0, rho0)
+        p = s.particles()
+        assert np.abs(p["r"] - parts.r).max() <= 1e-6
+        assert np.abs(p["v"] - parts.v).max() <= 1e-4 * 0.004
+    assert np.abs(parts.Fc).max() > 0
