@@ -2,8 +2,9 @@
 // bounce-back at the links into a sphere (Eq. UPI, Eq. LADDFLBE), the
 // momentum those links exchange summed in FP64 into each sphere's force and
 // torque (Eq. FORCEPP, Eq. FORCEPARTEQ, Eq. TORQUEPARTEQ), the leap-frog
-// update of Eq. PARDYN, and re-meshing of the nodes a moved sphere leaves or
-// reaches (the rule conserves the total momentum of fluid and spheres).
+// update of Eq. PARDYN with the spheres' contact and lubrication forces, and
+// re-meshing of the nodes a moved sphere leaves or reaches (the rule
+// conserves the total momentum of fluid and spheres).
 //
 // One block per sphere walks the cube of sites around its centre (half-width
 // ceil(R) + 2: every covered node, every fluid node linked to one, and every
@@ -82,8 +83,8 @@ __device__ __forceinline__ double disp(int x, int u, double c, int n) {
 
 // Is the site within radius of the centre? Far from the sphere's surface the
 // FP32 distance decides; near it, the exact FP64 test (the oracle's rule).
-__device__ __forceinline__ bool covered(const Cube& cube, const int (&u)[3], const int (&x)[3], float r2f,
-                                        const double* c, double R2, const Geom& g) {
+__device__ __forceinline__ bool covered(const int (&u)[3], const int (&x)[3], float r2f, const double* c, double R2,
+                                        const Geom& g) {
     const float R2f = (float)R2;
     if (r2f < 0.99f * R2f) return true;
     if (r2f > 1.01f * R2f) return false;
@@ -341,7 +342,7 @@ __global__ void __launch_bounds__(kPT) sphere_uncover_kernel(S* __restrict__ st,
         if (A.radius > 2.0 && r2 < in2) continue;   // deep inside: still covered
         const uint32_t s = site_of(x, g);
         if (A.owner[s] != q + 1) continue;
-        if (covered(cube, u, x, r2, c, R2, g)) continue;
+        if (covered(u, x, r2, c, R2, g)) continue;
         A.owner[s] = 0;
         A.moved[q] = 1;
         const double arm[3] = {disp(x[0], u[0], c[0], g.nx), disp(x[1], u[1], c[1], g.ny),
@@ -399,7 +400,7 @@ __global__ void __launch_bounds__(kPT) sphere_cover_kernel(S* __restrict__ st, c
         const float r2 = cube.dist2(u, df);
         margin = fminf(margin, fabsf(sqrtf(r2) - Rf));
         if (r2 < in2) continue;   // covered before the move too
-        if (!covered(cube, u, x, r2, c, R2, g)) continue;
+        if (!covered(u, x, r2, c, R2, g)) continue;
         const uint32_t s = site_of(x, g);
         if (A.owner[s] == q + 1) continue;   // covered before
         if ((mask && mask[s]) || atomicCAS(A.owner + s, 0, q + 1) != 0) {
