@@ -431,9 +431,64 @@ def time_e2e(W, prec, kernel, steps):
     return t1 - t0, h2d, d2h, bool(np.isfinite(oA).all())
 
 
-def time_adjoint(prec, kernel, n=128, steps=80, K=40, warmup=3):
+def precision_512(peak, peak_kind, steps=500, warmup=5):
+    """Precision form: the 512^3 spinodal run of `steps` steps with FP32,
+    FP16 and BF16 storage, each timed over all its steps (CUDA events), and
+    the max and RMS errors of the 16-bit runs' rho_A, rho_B and u against the
+    FP32 run (max|a - b| / max|b| and rms(a - b) / max|b| per field; u as a
+    vector field). The comparison with the FP64 oracle on the identical 64^3
+    seeded case is tests/test_gpu_precision.py."""
+    import torch
+    from paper_2112_08264_gb300 import Solver
+    W = workload("spinodal512")
+    n = 512
+    N = n ** 3
+    out, ref = {}, None
+    dA = torch.tensor(W["rA"], dtype=torch.float32, device="cuda")
+    dB = torch.tensor(W["rB"], dtype=torch.float32, device="cuda")
+    for prec in ("fp32", "fp16", "bf16"):
+        s = Solver(n, n, n, W["tau"], W["G"], prec=prec)
+        s.init(dA, dB)
+        s.step(warmup)
+        s.init(dA, dB)   # the measured run starts from the seeded state
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(s.stream):
+            e0.record(s.stream)
+            s.step(steps)
+            e1.record(s.stream)
+        e1.synchronize()
+        step_s = e0.elapsed_time(e1) / 1e3 / steps
+        rA, rB, u = s.moments()
+        s.close()
+        del s
+        torch.cuda.synchronize()
+        out[prec] = {"GLUPS": N / step_s / 1e9, "ms_per_step": step_s * 1e3, "steps": steps,
+                     "hbm_frac_of_%s" % peak_kind: BYTES_PER_SITE[prec] * N / step_s / 1e9 / peak}
+        if ref is None:
+            ref = (rA, rB, u)
+            continue
+        err = {}
+        for name, a, b in (("rho_A", rA, ref[0]), ("rho_B", rB, ref[1])):
+            d = (a.double() - b.double())
+            scale = float(b.abs().max())
+            err[name] = {"max": float(d.abs().max()) / scale, "rms": float(d.pow(2).mean().sqrt()) / scale}
+        du = (u.double() - ref[2].double())
+        uscale = float(ref[2].double().pow(2).sum(dim=0).sqrt().max())
+        err["u"] = {"max": float(du.abs().max()) / uscale, "rms": float(du.pow(2).mean().sqrt()) / uscale,
+                    "max_abs_u_fp32": uscale}
+        out[prec]["error_vs_fp32"] = err
+        del rA, rB, u, du
+    out["fp16_over_fp32"] = out["fp16"]["GLUPS"] / out["fp32"]["GLUPS"]
+    out["bf16_over_fp32"] = out["bf16"]["GLUPS"] / out["fp32"]["GLUPS"]
+    out["workload"] = W["desc"] + ", %d steps per precision" % steps
+    return out
+
+
+def time_adjoint(prec, kernel, n=128, steps=400, K=40, warmup=1):
     """Differentiation form: forward with checkpoints every K steps, then
-    lb_backward; returns per-step ms of both and their ratio."""
+    lb_backward; returns per-step ms of both, their ratio and the workspace
+    the recording needs."""
     import torch
     from paper_2112_08264_gb300 import Solver, inputs
     rA, rB = inputs.spinodal(n, n, n, seed=1234)
@@ -455,10 +510,12 @@ def time_adjoint(prec, kernel, n=128, steps=80, K=40, warmup=3):
         e2.synchronize()
         fwd.append(e0.elapsed_time(e1))
         bwd.append(e1.elapsed_time(e2))
+    ws = int(s.workspace.numel())
     s.close()
     f_ms, b_ms = fwd[-1] / steps, bwd[-1] / steps
-    return {"grid": [n, n, n], "steps": steps, "ckpt_every": K, "forward_ms_per_step": f_ms,
-            "backward_ms_per_step": b_ms, "backward_over_forward": b_ms / f_ms}
+    return {"grid": [n, n, n], "steps": steps, "ckpt_every": K, "checkpoints": steps // K + 1,
+            "forward_ms_per_step": f_ms, "backward_ms_per_step": b_ms, "backward_over_forward": b_ms / f_ms,
+            "workspace_bytes": ws}
 
 
 def oracle_sample(shape, tau, G, budget_s, min_steps=1, max_steps=1000, per_step_budget=None):
@@ -824,17 +881,7 @@ def main():
         if "fp16_fused" in var and args.prec == "fp32":
             line["fp16_over_fp32"] = var["fp16_fused"]["GLUPS"] / glups
         if args.config == "spinodal256" and args.grid is None:
-            W5 = workload("spinodal512")
-            N5 = 512 ** 3
-            c3 = {}
-            for prec in ("fp32", "fp16", "bf16"):
-                vms, _, _ = time_device(W5, prec, "fused", 100, 5)
-                vstep = vms / 1e3 / 100
-                c3[prec] = {"GLUPS": N5 / vstep / 1e9, "ms_per_step": vstep * 1e3,
-                            "hbm_frac_of_%s" % peak_kind: BYTES_PER_SITE[prec] * N5 / vstep / 1e9 / peak}
-            c3["fp16_over_fp32"] = c3["fp16"]["GLUPS"] / c3["fp32"]["GLUPS"]
-            line["precision_512"] = c3
-            del W5
+            line["precision_512"] = precision_512(peak, peak_kind)
             line["adjoint_128"] = time_adjoint("fp32", "fused")
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = run_cpu_baseline(W)

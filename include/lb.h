@@ -100,6 +100,14 @@ typedef struct {
     double cg_beta;        /* colour gradient: recolouring parameter, in [0, 1] */
     int max_particles;     /* > 0: room for that many moving spheres (lb_particles_set);
                               needs the Shan-Chen model, LB_KERNEL_FUSED, no recording */
+    int slab_halo;         /* > 0: the grid is one rank's slab of a lattice cut into
+                              z-slabs (Sec. 4, equal sub-domains exchanging their
+                              borders each step), extended by slab_halo ghost planes
+                              below and above that the caller fills from the
+                              neighbouring ranks (2 are needed: see lb_step_fluid).
+                              Every bounce-back link is then copied by lb_step_links,
+                              none inside the step kernel. Shan-Chen model, no
+                              spheres, no recording. 0 = a whole periodic lattice. */
 } lb_options;
 
 /* Fill *opt with the defaults above. */
@@ -145,6 +153,44 @@ lb_status lb_init(lb_ctx* ctx, const float* d_rhoA, const float* d_rhoB, const f
  * with bounce-back). Asynchronous on the context stream. When recording
  * (ckpt_every > 0) LB_ESTATE if the run would exceed ckpt_steps_max. */
 lb_status lb_step(lb_ctx* ctx, int n);
+
+/* One time step split in two, for a lattice cut into z-slabs over ranks
+ * (opt->slab_halo = 2; Sec. 4: equal sub-domains, border exchange every
+ * step). A rank holds its planes plus two ghost planes on each side. With
+ * the two border planes of each neighbour in its ghosts, the step computes
+ * every owned plane exactly as the whole lattice would (the force at a plane
+ * needs the densities of the planes next to it, which sum populations pulled
+ * from one plane further); the ghost planes come out wrong and the exchange
+ * replaces them. Per step:
+ *   lb_step_fluid(ctx)     the step kernel, without the bounce-back pass;
+ *   exchange               the caller copies planes [2, 4) of each rank into
+ *                          the upper ghosts [nz - 2, nz) of the rank below and
+ *                          planes [nz - 4, nz - 2) into the lower ghosts [0, 2)
+ *                          of the rank above (lb_planes gives their memory);
+ *   lb_step_links(ctx)     the write-side halfway bounce-back of every link
+ *                          (Eq. LADDFLBE at rest): a link whose source is a
+ *                          ghost node reads that node's exchanged value.
+ * lb_step(ctx, 1) is the two calls without the exchange. Between the two
+ * calls every other call on the context returns LB_ESTATE. After lb_init the
+ * caller exchanges once and calls lb_step_links before the first step.
+ * Every rank must give lb_init the same rho0_A, rho0_B (lb_options; e.g. the
+ * mean over the whole lattice) so that all ranks store the same deviations.
+ * Asynchronous on the context stream. */
+lb_status lb_step_fluid(lb_ctx* ctx);
+lb_status lb_step_links(lb_ctx* ctx);
+
+/* Device memory of planes [z0, z0 + nplanes) of the current state, in the
+ * library's internal storage (contiguous; valid until the next step): for
+ * copying border planes between ranks whose contexts have the same nx, ny,
+ * precision and rho0. *d_ptr is a DEVICE pointer into the workspace, *bytes
+ * its length. LB_EINVAL unless nx*ny is a multiple of 64 (planes must start
+ * on a storage block) and 0 <= z0, nplanes >= 1, z0 + nplanes <= nz. */
+lb_status lb_planes(lb_ctx* ctx, int z0, int nplanes, void** d_ptr, size_t* bytes);
+
+/* lb_stats over the fluid nodes of planes [z0, z0 + nplanes) only (a rank's
+ * owned planes; the totals of a decomposed lattice are their sum over the
+ * ranks). out5 is a HOST pointer. Synchronous. */
+lb_status lb_stats_planes(lb_ctx* ctx, int z0, int nplanes, double out5[5]);
 
 /* Moments of the current state into device fields: rho^A, rho^B (N floats
  * each, 0 at solid nodes) and, when d_u != NULL, the mixture velocity
@@ -260,7 +306,15 @@ lb_status lb_link_info(const lb_ctx* ctx, long long* listed, long long* in_tile,
  *   d_mask  DEVICE solid mask, N bytes, 1 = solid, or NULL (all fluid);
  *   G, body_force (HOST, 3 doubles, or NULL = 0) as in lb_create/lb_options;
  * into DEVICE outputs d_rhoA, d_rhoB (N floats) and d_u (3N floats SoA), any
- * of which may be NULL. It allocates nothing and calls no allocator: the
+ * of which may be NULL. The velocity always includes the Shan-Chen shift: for
+ * a colour-gradient state (whose velocity is sum_k sum_i c_i f_i^k / rho)
+ * pass G = 0 and body_force = NULL. d_mask must mark every node that holds no
+ * fluid (static solids and nodes covered by moving spheres); a node treated as
+ * fluid whose populations are all zero gets u = 0. The populations arrive as
+ * absolute FP32 values (about w_i rho each), so the moments carry their
+ * rounding: about 1e-8 absolute on rho^k and on u near rho = 1, where
+ * lb_moments, which sums the stored deviations from w_i rho0, resolves
+ * smaller differences. It allocates nothing and calls no allocator: the
  * neighbour-density scratch it needs is a static device array of 2^20 nodes
  * (8 MiB, held on every GPU that loads the library until the process exits).
  * N = nx*ny*nz above 2^20 is rejected with LB_EINVAL and a message in

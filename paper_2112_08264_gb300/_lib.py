@@ -29,6 +29,7 @@ class LbOptions(ctypes.Structure):
         ("cg_sigma", ctypes.c_double),
         ("cg_beta", ctypes.c_double),
         ("max_particles", ctypes.c_int),
+        ("slab_halo", ctypes.c_int),
     ]
 
 
@@ -86,6 +87,10 @@ def lib():
     L.lb_moments_noalloc.argtypes = ([ctypes.c_int] * 3 + [ctypes.c_float, ctypes.POINTER(ctypes.c_double),
                                                              _FP, _VP, _FP, _FP, _FP, _VP])
     L.lb_moments_noalloc.restype = ctypes.c_int
+    L.lb_step_fluid.argtypes = [_VP]
+    L.lb_step_links.argtypes = [_VP]
+    L.lb_planes.argtypes = [_VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_VP), ctypes.POINTER(ctypes.c_size_t)]
+    L.lb_stats_planes.argtypes = [_VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     L.lb_destroy.argtypes = [_VP]
     L.lb_destroy.restype = None
     L.lb_status_str.argtypes = [ctypes.c_int]
@@ -95,7 +100,8 @@ def lib():
     for name in ("lb_create", "lb_set_stream", "lb_init", "lb_step", "lb_moments", "lb_stats",
                  "lb_get_state", "lb_set_state", "lb_backward", "lb_launch_info", "lb_link_info",
                  "lb_particles_set", "lb_particles_get", "lb_particles_contact",
-                 "lb_particles_lubrication"):
+                 "lb_particles_lubrication", "lb_step_fluid", "lb_step_links", "lb_planes",
+                 "lb_stats_planes"):
         getattr(L, name).restype = ctypes.c_int
     # one-component BGK (include/lb1.h)
     L.lb1_workspace_bytes.argtypes = [ctypes.c_int] * 4
@@ -124,7 +130,7 @@ def check(status, what):
 
 
 def options(prec="fp32", kernel="fused", rho0=(0.0, 0.0), body_force=(0.0, 0.0, 0.0),
-            ckpt_every=0, ckpt_steps_max=0, model="shan_chen", cg=None, max_particles=0):
+            ckpt_every=0, ckpt_steps_max=0, model="shan_chen", cg=None, max_particles=0, slab_halo=0):
     """lb_options; ``cg`` = dict(nu=(nu_A, nu_B), sigma=, beta=) for the
     colour-gradient model."""
     o = LbOptions()
@@ -142,6 +148,7 @@ def options(prec="fp32", kernel="fused", rho0=(0.0, 0.0), body_force=(0.0, 0.0, 
     o.ckpt_every = int(ckpt_every)
     o.ckpt_steps_max = int(ckpt_steps_max)
     o.max_particles = int(max_particles)
+    o.slab_halo = int(slab_halo)
     return o
 
 

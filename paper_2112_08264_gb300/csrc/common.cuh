@@ -14,6 +14,7 @@
 #include <cstdint>
 #include "lattice.cuh"
 #include "store.cuh"
+#include "vec2.cuh"
 
 namespace lbgb {
 
@@ -177,32 +178,97 @@ __device__ __forceinline__ void pull(const S* __restrict__ src, const Geom& g, c
     });
 }
 
-__device__ __forceinline__ float dens_sum(const float (&d)[Q]) {
-    float s = 0.f;
+// Density deviations drho^k = rho^k - rho0^k = sum_i d_i^k and momentum
+// j = sum_k sum_i c_i d_i^k (sum_i c_i w_i rho0 = 0, so the deviations carry
+// the whole momentum), in velocity order starting from d_0. The momentum is
+// summed over opposite pairs, c_i (d_i - d_opp(i)), whose differences are
+// exact when the two are close.
+//
+// Two forms. With 16-bit storage the node work is bound by instruction issue,
+// and the sums take both components at once as (A, B) pairs with the packed
+// FP32 instructions (a component's momentum is summed on its own and the two
+// are added last). With FP32 storage (bound by memory bandwidth, and
+// scheduled best as it is) every sum is a scalar chain with A and B added
+// per pair. Every kernel of one storage type takes the same form, so the
+// kernels of one precision give the same bits.
+template <typename S>
+constexpr bool kPackedSums = sizeof(S) == 2;
+
+__device__ __forceinline__ float2 dens_sum2(const float2 (&d)[Q]) {
+    float2 s = d[0];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) s += d[i];
+    for (int i = 1; i < Q; ++i) s = add2(s, d[i]);
+    return s;
+}
+// one component: the same additions in the same order
+__device__ __forceinline__ float dens_sum(const float (&d)[Q]) {
+    float s = d[0];
+#pragma unroll
+    for (int i = 1; i < Q; ++i) s = __fadd_rn(s, d[i]);
     return s;
 }
 
-// Density deviations drho^k = rho^k - rho0^k = sum_i d_i^k and momentum
-// j = sum_k sum_i c_i d_i^k (sum_i c_i w_i rho0 = 0, so the deviations carry
-// the whole momentum). The momentum is summed over opposite pairs,
-// c_i (d_i - d_opp(i)), whose differences are exact when the two are close.
-__device__ __forceinline__ void momentum(const float (&d)[2][Q], float (&j)[3]) {
-    j[0] = j[1] = j[2] = 0.f;
-    static_for<0, 9>([&](auto M) {
-        constexpr int i = 2 * decltype(M)::value + 1;   // (i, i + 1) are opposite
-        const float diff = (d[0][i] - d[0][i + 1]) + (d[1][i] - d[1][i + 1]);
-        if constexpr (Vel<i>::x != 0) j[0] += Vel<i>::x * diff;
-        if constexpr (Vel<i>::y != 0) j[1] += Vel<i>::y * diff;
-        if constexpr (Vel<i>::z != 0) j[2] += Vel<i>::z * diff;
-    });
+// c_i along axis a for a velocity known at compile time
+template <int i, int a>
+__host__ __device__ constexpr int vel_comp() {
+    return a == 0 ? Vel<i>::x : (a == 1 ? Vel<i>::y : Vel<i>::z);
+}
+// first and second axes along which a velocity moves (diagonals move along two)
+template <int i>
+__host__ __device__ constexpr int vel_axis0() {
+    return Vel<i>::x != 0 ? 0 : (Vel<i>::y != 0 ? 1 : 2);
+}
+template <int i>
+__host__ __device__ constexpr int vel_axis1() {
+    return (Vel<i>::x != 0 && Vel<i>::y != 0) ? 1 : 2;
 }
 
+template <bool PACKED>
+__device__ __forceinline__ void momentum2(const float2 (&d)[Q], float (&j)[3]) {
+    if constexpr (!PACKED) {
+        j[0] = j[1] = j[2] = 0.f;
+        static_for<0, 9>([&](auto M) {
+            constexpr int i = 2 * decltype(M)::value + 1;   // (i, i + 1) are opposite
+            const float diff = (d[i].x - d[i + 1].x) + (d[i].y - d[i + 1].y);
+            if constexpr (Vel<i>::x != 0) j[0] += Vel<i>::x * diff;
+            if constexpr (Vel<i>::y != 0) j[1] += Vel<i>::y * diff;
+            if constexpr (Vel<i>::z != 0) j[2] += Vel<i>::z * diff;
+        });
+    } else {
+        float2 J[3];
+        static_for<0, 9>([&](auto M) {
+            constexpr int i = 2 * decltype(M)::value + 1;
+            // the odd member of each pair moves + along its first axis (public order)
+            static_assert(vel_comp<i, vel_axis0<i>()>() == 1, "velocity order: odd members lead");
+            const float2 diff = sub2(d[i], d[i + 1]);
+            constexpr int a0 = vel_axis0<i>();
+            if constexpr (Vel<i>::c2 == 1) {
+                J[a0] = diff;   // the axis pairs come first (i = 1, 3, 5)
+            } else {
+                constexpr int a1 = vel_axis1<i>();
+                J[a0] = add2(J[a0], diff);
+                if constexpr (vel_comp<i, a1>() > 0) J[a1] = add2(J[a1], diff);
+                else J[a1] = sub2(J[a1], diff);
+            }
+        });
+#pragma unroll
+        for (int a = 0; a < 3; ++a) j[a] = __fadd_rn(J[a].x, J[a].y);
+    }
+}
+
+template <typename S>
+__device__ __forceinline__ void momentum(const float (&d)[2][Q], float (&j)[3]) {
+    float2 d2[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) d2[i] = make_float2(d[0][i], d[1][i]);
+    momentum2<kPackedSums<S>>(d2, j);
+}
+
+template <typename S>
 __device__ __forceinline__ void sums(const float (&d)[2][Q], float& dA, float& dB, float (&j)[3]) {
     dA = dens_sum(d[0]);
     dB = dens_sum(d[1]);
-    momentum(d, j);
+    momentum<S>(d, j);
 }
 
 // BGK collision with the Shan-Chen velocity shift, in deviation form, and
@@ -402,24 +468,29 @@ struct PlaneSums {
     float2 dx, dy, t;
 };
 
+// both components at once, with packed (A, B) instructions
+
 __device__ __forceinline__ PlaneSums plane_sums(float2 c, float2 xp, float2 xm, float2 yp, float2 ym) {
     PlaneSums s;
-    s.dx = make_float2(xp.x - xm.x, xp.y - xm.y);
-    s.dy = make_float2(yp.x - ym.x, yp.y - ym.y);
-    s.t = make_float2(kW1 * c.x + kW2 * ((xp.x + xm.x) + (yp.x + ym.x)),
-                      kW1 * c.y + kW2 * ((xp.y + xm.y) + (yp.y + ym.y)));
+    s.dx = sub2(xp, xm);
+    s.dy = sub2(yp, ym);
+    s.t = fma2(splat(kW1), c, mul2(splat(kW2), add2(add2(xp, xm), add2(yp, ym))));
     return s;
 }
 
 __device__ __forceinline__ void force_sums(const PlaneSums& lo, const PlaneSums& mid, const PlaneSums& hi,
                                            float2 pp, float2 mp, float2 pm, float2 mm, float (&SA)[3],
                                            float (&SB)[3]) {
-    SA[0] = (kW1 * mid.dx.x + kW2 * ((pp.x - mp.x) + (pm.x - mm.x))) + kW2 * (hi.dx.x + lo.dx.x);
-    SB[0] = (kW1 * mid.dx.y + kW2 * ((pp.y - mp.y) + (pm.y - mm.y))) + kW2 * (hi.dx.y + lo.dx.y);
-    SA[1] = (kW1 * mid.dy.x + kW2 * ((pp.x - pm.x) + (mp.x - mm.x))) + kW2 * (hi.dy.x + lo.dy.x);
-    SB[1] = (kW1 * mid.dy.y + kW2 * ((pp.y - pm.y) + (mp.y - mm.y))) + kW2 * (hi.dy.y + lo.dy.y);
-    SA[2] = hi.t.x - lo.t.x;
-    SB[2] = hi.t.y - lo.t.y;
+    const float2 w1 = splat(kW1), w2 = splat(kW2);
+    const float2 sx = fma2(w2, add2(hi.dx, lo.dx), fma2(w1, mid.dx, mul2(w2, add2(sub2(pp, mp), sub2(pm, mm)))));
+    const float2 sy = fma2(w2, add2(hi.dy, lo.dy), fma2(w1, mid.dy, mul2(w2, add2(sub2(pp, pm), sub2(mp, mm)))));
+    const float2 sz = sub2(hi.t, lo.t);
+    SA[0] = sx.x;
+    SB[0] = sx.y;
+    SA[1] = sy.x;
+    SB[1] = sy.y;
+    SA[2] = sz.x;
+    SB[2] = sz.y;
 }
 
 // plane quantities of plane dz (-1, 0, +1) from a lookup of dpsi(dx, dy, dz)
@@ -429,10 +500,11 @@ __device__ __forceinline__ PlaneSums plane_sums_at(Look&& psi, int dz) {
 }
 
 // S^k from a lookup of dpsi(dx, dy, dz) (the 18 neighbours of the node).
-// FACTORED: the plane form above (16-bit storage, whose box kernel reuses
-// the plane quantities); otherwise one multiply-add per link and component in
-// velocity order (FP32, where it schedules faster). Every kernel of a storage
-// type uses the same form, so the kernels of one precision give the same bits.
+// FACTORED: the plane form above with packed (A, B) instructions (16-bit
+// storage, whose box kernel reuses the plane quantities); otherwise one
+// multiply-add per link and component in velocity order (FP32, where it
+// schedules faster). Every kernel of a storage type uses the same form, so
+// the kernels of one precision give the same bits.
 template <bool FACTORED, typename Look>
 __device__ __forceinline__ void neighbour_sums(Look&& psi, float (&SA)[3], float (&SB)[3]) {
     if constexpr (FACTORED) {

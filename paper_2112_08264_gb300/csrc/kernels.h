@@ -61,6 +61,10 @@ struct StepLaunch {
 };
 
 cudaError_t launch_step(const StepLaunch& L, cudaStream_t st);
+// The two parts of launch_step: the step kernel(s), and the write-side
+// bounce-back pass of a masked grid (nothing without a mask).
+cudaError_t launch_step_fluid(const StepLaunch& L, cudaStream_t st);
+cudaError_t launch_step_links(const StepLaunch& L, cudaStream_t st);
 
 // Register fused kernel: launch geometry for a grid on a device with sm_count SMs.
 void fused_geometry(int nx, int ny, int nz, int sm_count, int* tiles, int* zsplit, int* threads);
@@ -153,10 +157,11 @@ cudaError_t launch_moments(int prec, const void* src, const uint32_t* flags, con
                            float* rhoA, float* rhoB, float* u, const Geom& g, const Phys& p,
                            cudaStream_t st);
 
-// FP64 conserved totals: partials[kRedBlocks][kRedVals] then out[kRedVals] =
-// {mass A, mass B, Px, Py, Pz, non-finite count}.
+// FP64 conserved totals over the sites [s0, s1) (s1 < 0: to the end):
+// partials[kRedBlocks][kRedVals] then out[kRedVals] = {mass A, mass B, Px,
+// Py, Pz, non-finite count}.
 cudaError_t launch_stats(int prec, const void* src, const uint32_t* flags, double* partials, double* out,
-                         const Geom& g, const Phys& p, cudaStream_t st);
+                         const Geom& g, const Phys& p, cudaStream_t st, long long s0 = 0, long long s1 = -1);
 
 // Checks of lb_init inputs over fluid nodes: out = {sum rhoA, sum rhoB,
 // fluid count, bad count, 0, 0}. Bad: not finite, or rho^k <= 0 (Shan-Chen

@@ -65,6 +65,9 @@ bool valid_options(const lb_options& o) {
         (o.model != LB_MODEL_SHAN_CHEN || o.kernel != LB_KERNEL_FUSED || o.ckpt_every != 0))
         return false;
     if (o.ckpt_every > 0 && o.ckpt_steps_max < 1) return false;
+    if (o.slab_halo < 0) return false;
+    if (o.slab_halo > 0 && (o.model != LB_MODEL_SHAN_CHEN || o.max_particles > 0 || o.ckpt_every != 0))
+        return false;
     if (o.model != LB_MODEL_SHAN_CHEN && o.model != LB_MODEL_COLOUR_GRADIENT) return false;
     if (o.model == LB_MODEL_COLOUR_GRADIENT) {
         if (!(std::isfinite(o.cg_nu_A) && o.cg_nu_A > 0.0 && std::isfinite(o.cg_nu_B) && o.cg_nu_B > 0.0))
@@ -140,6 +143,7 @@ struct lb_ctx {
     // recording for the adjoint
     bool recording;       // lb_init was called with ckpt_every > 0 and the run is intact
     double rho0_d[2];
+    bool links_pending;   // lb_step_fluid ran; lb_step_links completes the step
 };
 
 namespace {
@@ -276,8 +280,8 @@ lb_status lb_create(int nx, int ny, int nz, float tau, float G, const uint8_t* m
         e = cudaMemcpyAsync(c->mask_dev, mask, (size_t)c->g.N, cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess) e = launch_flags(c->mask_dev, c->flags, c->g, c->stream);
         // tile lists for the box kernel's tiling (counters in the density scratch)
-        TileMap map;
-        if (c->plan.box && c->plan.R > 0) {
+        TileMap map;   // a slab's links all go to the pass after the exchange (no tile lists)
+        if (c->plan.box && c->plan.R > 0 && o.slab_halo == 0) {
             map.ncols = c->plan.ncols;
             map.R = c->plan.R;
             map.zchunk = c->plan.zchunk;
@@ -348,6 +352,7 @@ lb_status lb_init(lb_ctx* c, const float* rA, const float* rB, const float* u) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_status("init", e);
     c->initialized = true;
+    c->links_pending = false;
     c->steps = 0;
     c->recording = c->opt.ckpt_every > 0 && u == nullptr;
     return LB_OK;
@@ -384,6 +389,7 @@ int reflect_launches(const lb_ctx* c) {
 lb_status lb_step(lb_ctx* c, int n) {
     if (!c || n < 1) return LB_EINVAL;
     if (!c->initialized) return LB_ESTATE;
+    if (c->links_pending) return LB_ESTATE;
     const int K = c->opt.ckpt_every;
     if (K > 0 && c->recording && c->steps + n > c->opt.ckpt_steps_max) return LB_ESTATE;
     StepLaunch S = step_launch(c);
@@ -410,9 +416,60 @@ lb_status lb_step(lb_ctx* c, int n) {
     return LB_OK;
 }
 
+lb_status lb_step_fluid(lb_ctx* c) {
+    if (!c) return LB_EINVAL;
+    if (!c->initialized || c->links_pending || c->particles || c->opt.ckpt_every > 0) return LB_ESTATE;
+    StepLaunch S = step_launch(c);
+    S.src = c->pop[c->cur];
+    S.dst = c->pop[1 - c->cur];
+    const cudaError_t e = launch_step_fluid(S, c->stream);
+    if (e != cudaSuccess) return cuda_status("step", e);
+    c->cur ^= 1;
+    c->steps += 1;
+    c->links_pending = c->has_mask;
+    return LB_OK;
+}
+
+lb_status lb_step_links(lb_ctx* c) {
+    if (!c) return LB_EINVAL;
+    if (!c->initialized) return LB_ESTATE;
+    c->links_pending = false;
+    if (!c->has_mask) return LB_OK;
+    StepLaunch S = step_launch(c);
+    S.dst = c->pop[c->cur];
+    return cuda_status("links", launch_step_links(S, c->stream));
+}
+
+lb_status lb_planes(lb_ctx* c, int z0, int nplanes, void** d_ptr, size_t* bytes) {
+    if (!c || !d_ptr || !bytes) return LB_EINVAL;
+    if (c->g.plane % kBlk != 0 || z0 < 0 || nplanes < 1 || (long long)z0 + nplanes > c->g.nz) return LB_EINVAL;
+    const size_t plane_bytes = (size_t)(c->g.plane / kBlk) * (2 * Q * kBlk) * store_bytes(c->opt.prec);
+    *d_ptr = static_cast<char*>(c->pop[c->cur]) + (size_t)z0 * plane_bytes;
+    *bytes = (size_t)nplanes * plane_bytes;
+    return LB_OK;
+}
+
+lb_status lb_stats_planes(lb_ctx* c, int z0, int nplanes, double out5[5]) {
+    if (!c || !out5 || z0 < 0 || nplanes < 1 || (long long)z0 + nplanes > c->g.nz) return LB_EINVAL;
+    if (!c->initialized || c->links_pending) return LB_ESTATE;
+    Phys rp;
+    cudaError_t e = reader_phys(c, rp);
+    if (e == cudaSuccess)
+        e = launch_stats(c->opt.prec, c->pop[c->cur], flags_of(c), c->red_part, c->red_out, c->g, rp, c->stream,
+                         (long long)z0 * c->g.plane, ((long long)z0 + nplanes) * c->g.plane);
+    if (e != cudaSuccess) return cuda_status("reduction launch", e);
+    double red[kRedVals];
+    e = cudaMemcpyAsync(red, c->red_out, kRedVals * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_status("reduction", e);
+    for (int q = 0; q < 5; ++q) out5[q] = red[q];
+    return red[5] > 0.0 ? LB_ENONFINITE : LB_OK;
+}
+
 lb_status lb_moments(lb_ctx* c, float* rA, float* rB, float* u) {
     if (!c) return LB_EINVAL;
     if (!c->initialized) return LB_ESTATE;
+    if (c->links_pending) return LB_ESTATE;
     const uint32_t* fl = flags_of(c);
     Phys rp;
     cudaError_t e = reader_phys(c, rp);
@@ -425,6 +482,7 @@ lb_status lb_moments(lb_ctx* c, float* rA, float* rB, float* u) {
 lb_status lb_stats(lb_ctx* c, double out5[5]) {
     if (!c || !out5) return LB_EINVAL;
     if (!c->initialized) return LB_ESTATE;
+    if (c->links_pending) return LB_ESTATE;
     double red[kRedVals];
     lb_status s = run_reduction(c, red, true);
     if (s != LB_OK) return s;
@@ -435,6 +493,7 @@ lb_status lb_stats(lb_ctx* c, double out5[5]) {
 lb_status lb_get_state(lb_ctx* c, float* dst) {
     if (!c || !dst) return LB_EINVAL;
     if (!c->initialized) return LB_ESTATE;
+    if (c->links_pending) return LB_ESTATE;
     Phys rp;
     cudaError_t e = reader_phys(c, rp);
     if (e == cudaSuccess) e = launch_get_state(c->opt.prec, c->pop[c->cur], flags_of(c), dst, c->g, rp, c->stream);
@@ -444,6 +503,7 @@ lb_status lb_get_state(lb_ctx* c, float* dst) {
 lb_status lb_set_state(lb_ctx* c, const float* src) {
     if (!c || !src) return LB_EINVAL;
     if (!c->initialized) return LB_ESTATE;
+    if (c->links_pending) return LB_ESTATE;
     c->recording = false;   // the recorded trajectory no longer leads to this state
     return cuda_status("set_state", launch_unstream(c->opt.prec, c->pop[c->cur], flags_of(c),
                                                     src, nullptr, nullptr, nullptr, c->g, c->p, c->stream));

@@ -338,7 +338,7 @@ __global__ void moments_kernel(const S* __restrict__ src, const uint32_t* __rest
     float d[2][Q];
     pull<S, MASK>(src, g, P, p.slots ? 0u : fl, d);
     float dA, dB, j[3];
-    sums(d, dA, dB, j);
+    sums<S>(d, dA, dB, j);
     const float rA = p.rho0[0] + dA, rB = p.rho0[1] + dB;
     if (oA) oA[s] = rA;
     if (oB) oB[s] = rB;
@@ -372,10 +372,10 @@ __global__ void moments_kernel(const S* __restrict__ src, const uint32_t* __rest
 template <typename S, bool MASK>
 __global__ void __launch_bounds__(256)
 stats_kernel(const S* __restrict__ src, const uint32_t* __restrict__ flags, double* __restrict__ partials,
-             Geom g, Phys p) {
+             Geom g, Phys p, long long s0, long long s1) {
     double v[kRedVals] = {0, 0, 0, 0, 0, 0};
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.N; s += stride) {
+    for (long long s = s0 + (long long)blockIdx.x * blockDim.x + threadIdx.x; s < s1; s += stride) {
         int x, y, z;
         site_xyz(s, g, x, y, z);
         uint32_t fl = 0;
@@ -389,7 +389,7 @@ stats_kernel(const S* __restrict__ src, const uint32_t* __restrict__ flags, doub
         pull<S, MASK>(src, g, P, p.slots ? 0u : fl, d);
         // per-node sums in FP32 (19 terms), accumulated across nodes in FP64
         float dA, dB, j[3];
-        sums(d, dA, dB, j);
+        sums<S>(d, dA, dB, j);
         v[0] += (double)p.rho0[0] + (double)dA;
         v[1] += (double)p.rho0[1] + (double)dB;
         v[2] += (double)j[0];
@@ -590,11 +590,15 @@ cudaError_t launch_moments(int prec, const void* src, const uint32_t* flags, con
 }
 
 cudaError_t launch_stats(int prec, const void* src, const uint32_t* flags, double* partials, double* out,
-                         const Geom& g, const Phys& p, cudaStream_t st) {
-#define LBGB_STATS(T)                                                                              \
-    [&] {                                                                                          \
-        if (flags) stats_kernel<T, true><<<kRedBlocks, 256, 0, st>>>((const T*)src, flags, partials, g, p); \
-        else stats_kernel<T, false><<<kRedBlocks, 256, 0, st>>>((const T*)src, flags, partials, g, p);      \
+                         const Geom& g, const Phys& p, cudaStream_t st, long long s0, long long s1) {
+    if (s1 < 0 || s1 > g.N) s1 = g.N;
+    if (s0 < 0) s0 = 0;
+#define LBGB_STATS(T)                                                                                       \
+    [&] {                                                                                                   \
+        if (flags)                                                                                          \
+            stats_kernel<T, true><<<kRedBlocks, 256, 0, st>>>((const T*)src, flags, partials, g, p, s0, s1); \
+        else                                                                                                \
+            stats_kernel<T, false><<<kRedBlocks, 256, 0, st>>>((const T*)src, flags, partials, g, p, s0, s1); \
     }
     cudaError_t e = by_prec(prec, LBGB_STATS(float), LBGB_STATS(__half), LBGB_STATS(__nv_bfloat16));
 #undef LBGB_STATS

@@ -182,7 +182,7 @@ fused_async_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_
             const int sm_m = (e - 2) & 3, sm_c = (e - 1) & 3, sm_p = e & 3;
             if (!solid_cur) {
                 float dA, dB, j[3];
-                sums(cur, dA, dB, j);
+                sums<S>(cur, dA, dB, j);
                 float SA[3], SB[3];
                 neighbour_sums<kFactoredSums<S>>(
                     [&](int dx, int dy, int dz) {
@@ -383,23 +383,40 @@ fused_box_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t*
         if (MASK && (fl & kSolid)) return make_float2(-p.rho0[0], -p.rho0[1]);
         return make_float2(dens_sum(d[0]), dens_sum(d[1]));
     };
+    // density deviations of a node whose populations are not kept (16-bit
+    // storage: both components summed at once)
+    auto read_density = [&](int st, int lx, int ly) -> float2 {
+        if constexpr (sizeof(S) == 2) {
+            if (MASK && (stage_flags(st)[(ly + 1) * 40 + lx + 4] & kSolid)) return make_float2(-p.rho0[0], -p.rho0[1]);
+            const S* nb = stage_base(st) + (ly + 1) * B::ROW + (lx + B::PAD) * 2;
+            float2 d[Q];
+            static_for<0, Q>([&](auto II) {
+                constexpr int i = decltype(II)::value;
+                d[i] = Store<S>::lds2v(nb + i * B::VS - 2 * Vel<i>::x);
+            });
+            return dens_sum2(d);
+        } else {
+            float d[2][Q];
+            uint32_t fl;
+            return read_node(st, lx, ly, d, fl);
+        }
+    };
     // 16-bit storage, own node: the pairs stay packed (one word per velocity)
     // until the collision; the momentum is taken here, from the same values
     auto read_node_packed = [&](int st, int lx, int ly, uint32_t (&w)[Q], float (&j)[3], uint32_t& fl) -> float2 {
         fl = MASK ? stage_flags(st)[(ly + 1) * 40 + lx + 4] : 0u;
         const S* nb = stage_base(st) + (ly + 1) * B::ROW + (lx + B::PAD) * 2;
-        float d[2][Q];
+        float2 d[Q];
         static_for<0, Q>([&](auto II) {
             if constexpr (sizeof(S) == 2) {
                 constexpr int i = decltype(II)::value;
                 w[i] = *reinterpret_cast<const uint32_t*>(nb + i * B::VS - 2 * Vel<i>::x);
-                d[0][i] = Store<S>::part(w[i], 0);
-                d[1][i] = Store<S>::part(w[i], 1);
+                d[i] = Store<S>::unpack2(w[i]);
             }
         });
-        momentum(d, j);
+        momentum2<kPackedSums<S>>(d, j);
         if (MASK && (fl & kSolid)) return make_float2(-p.rho0[0], -p.rho0[1]);
-        return make_float2(dens_sum(d[0]), dens_sum(d[1]));
+        return dens_sum2(d);
     };
 
     // 16-bit storage (three or four stages fit): the copies of event
@@ -464,11 +481,7 @@ fused_box_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t*
                 ring[slot * RH * RW + own_off] = ring_val(read_node(st_cur, tx, ty, nxt.d, nxt.fl));
             }
         }
-        if (has_halo) {
-            float dh[2][Q];
-            uint32_t fh;
-            ring_at(slot, hly, hlx) = ring_val(read_node(st_cur, hlx, hly, dh, fh));
-        }
+        if (has_halo) ring_at(slot, hly, hlx) = ring_val(read_density(st_cur, hlx, hly));
         __syncthreads();   // ring of plane e complete; stage st_cur fully read
         if constexpr (!early) issue(e + ahead, z_iss, st_cur);
         if (kLinks && !kLateStore && links && e >= 4) store_links(e - 4);
@@ -487,7 +500,7 @@ fused_box_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t*
             const float2* rc = ring + ((e - 1) & 3) * RH * RW + own_off;
             float dA, dB, j[3];
             if constexpr (!packed) {
-                sums(cur.d, dA, dB, j);
+                sums<S>(cur.d, dA, dB, j);
             } else {   // own density deviations are already in the ring (same sums)
                 dA = CG ? cur.dd.x : rc[0].x;
                 dB = CG ? cur.dd.y : rc[0].y;

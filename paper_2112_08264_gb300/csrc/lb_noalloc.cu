@@ -81,6 +81,10 @@ __global__ void psi_kernel(const float* __restrict__ f, const uint8_t* __restric
 
 // rho^k = sum_i f_i^k and u = (sum_k sum_i c_i f_i^k + (F^A + F^B)/2) / rho,
 // F^A = -G psi^A sum_i w_i psi^B(x + c_i) c_i + rho^A g (and A <-> B).
+// The momentum is summed over opposite pairs, c_i (f_i - f_opp(i)), whose
+// differences are exact for the close values of a near-rest node. A node
+// treated as fluid whose populations are all zero (a covered node of a state
+// exported without its sphere coverage) has no velocity: u = 0 there.
 __global__ void moments_from_f_kernel(const float* __restrict__ f, const uint8_t* __restrict__ mask,
                                       const float* __restrict__ psi, float* __restrict__ oA,
                                       float* __restrict__ oB, float* __restrict__ ou, Geom g, float G,
@@ -96,14 +100,20 @@ __global__ void moments_from_f_kernel(const float* __restrict__ f, const uint8_t
     int x, y, z;
     node_xyz(s, g, x, y, z);
     float rA = 0.f, rB = 0.f, j[3] = {0.f, 0.f, 0.f};
+    float fa[Q], fb[Q];
     static_for<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        const float a = f[(size_t)i * g.N + s], b = f[(size_t)(Q + i) * g.N + s];
-        rA += a;
-        rB += b;
-        if constexpr (Vel<i>::x != 0) j[0] += Vel<i>::x * (a + b);
-        if constexpr (Vel<i>::y != 0) j[1] += Vel<i>::y * (a + b);
-        if constexpr (Vel<i>::z != 0) j[2] += Vel<i>::z * (a + b);
+        fa[i] = f[(size_t)i * g.N + s];
+        fb[i] = f[(size_t)(Q + i) * g.N + s];
+        rA += fa[i];
+        rB += fb[i];
+    });
+    static_for<0, 9>([&](auto M) {
+        constexpr int i = 2 * decltype(M)::value + 1;   // (i, i + 1) are opposite
+        const float diff = (fa[i] - fa[i + 1]) + (fb[i] - fb[i + 1]);
+        if constexpr (Vel<i>::x != 0) j[0] += Vel<i>::x * diff;
+        if constexpr (Vel<i>::y != 0) j[1] += Vel<i>::y * diff;
+        if constexpr (Vel<i>::z != 0) j[2] += Vel<i>::z * diff;
     });
     if (oA) oA[s] = rA;
     if (oB) oB[s] = rB;
@@ -119,6 +129,10 @@ __global__ void moments_from_f_kernel(const float* __restrict__ f, const uint8_t
         },
         SA, SB);
     const float gv[3] = {gx, gy, gz};
+    if (rA + rB == 0.f) {
+        ou[s] = ou[g.N + s] = ou[2 * g.N + s] = 0.f;
+        return;
+    }
     const float inv = 1.0f / (rA + rB);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -135,12 +149,14 @@ extern "C" lb_status lb_moments_noalloc(int nx, int ny, int nz, float G, const d
                                         float* d_u, void* stream) {
     using namespace lbgb;
     if (nx < 3 || ny < 3 || nz < 3 || !d_f || !std::isfinite(G)) return LB_EINVAL;
-    const long long N = (long long)nx * ny * nz;
+    // each side alone within the limit first, so that the product cannot overflow
+    const bool side_ok = nx <= kMaxNodes && ny <= kMaxNodes && nz <= kMaxNodes;
+    const long long N = side_ok ? (long long)nx * ny * nz : kMaxNodes + 1;
     if (N > kMaxNodes) {   // beyond the static scratch
         char msg[160];
         std::snprintf(msg, sizeof msg,
-                      "lb_moments_noalloc: nx*ny*nz = %lld exceeds the static scratch limit of %lld nodes",
-                      N, kMaxNodes);
+                      "lb_moments_noalloc: nx*ny*nz = %d*%d*%d exceeds the static scratch limit of %lld nodes",
+                      nx, ny, nz, kMaxNodes);
         record_error_text(msg);
         return LB_EINVAL;
     }

@@ -106,7 +106,7 @@ fused_step_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t
         // collide plane z
         if (active && (!MASK || !(fl_cur & kSolid))) {
             float dA, dB, j[3];
-            sums(cur, dA, dB, j);
+            sums<S>(cur, dA, dB, j);
             float SA[3], SB[3];
             neighbour_sums<kFactoredSums<S>>(
                 [&](int dx, int dy, int dz) {
@@ -161,7 +161,7 @@ collide_kernel(const S* __restrict__ src, S* __restrict__ dst, const uint32_t* _
     float d[2][Q];
     pull<S, MASK>(src, g, P, fl, d);
     float dA, dB, j[3];
-    sums(d, dA, dB, j);
+    sums<S>(d, dA, dB, j);
     float SA[3], SB[3];
     const bool cg = p.model == 1;   // colour gradient: the neighbour sums of Theta
     neighbour_sums<kFactoredSums<S>>(
@@ -227,10 +227,17 @@ bool tiles_in_kernel(const StepLaunch& L) {
            L.plan.box && k.map.ncols == L.plan.ncols && k.map.R == L.plan.R && k.map.zchunk == L.plan.zchunk;
 }
 
-cudaError_t launch_step(const StepLaunch& L, cudaStream_t st) {
-    const cudaError_t e = launch_step_kernels(L, st);
-    if (e != cudaSuccess || L.flags == nullptr) return e;
+cudaError_t launch_step_fluid(const StepLaunch& L, cudaStream_t st) { return launch_step_kernels(L, st); }
+
+cudaError_t launch_step_links(const StepLaunch& L, cudaStream_t st) {
+    if (L.flags == nullptr) return cudaSuccess;
     return launch_reflect(L.prec, L.dst, L.flags, L.links, !tiles_in_kernel(L), L.g, st);
+}
+
+cudaError_t launch_step(const StepLaunch& L, cudaStream_t st) {
+    const cudaError_t e = launch_step_fluid(L, st);
+    if (e != cudaSuccess) return e;
+    return launch_step_links(L, st);
 }
 
 void fused_geometry(int nx, int ny, int nz, int sm_count, int* tiles, int* zsplit, int* threads) {

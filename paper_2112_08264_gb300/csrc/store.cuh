@@ -36,6 +36,8 @@ template <> struct Store<float> {
     static __device__ __forceinline__ void st2(float* p, float a, float b) {
         __stcs(reinterpret_cast<float2*>(p), make_float2(a, b));
     }
+    // the pair as (A, B), from shared memory
+    static __device__ __forceinline__ float2 lds2v(const float* p) { return *reinterpret_cast<const float2*>(p); }
 };
 
 template <> struct Store<__half> {
@@ -63,6 +65,13 @@ template <> struct Store<__half> {
     }
     static __device__ __forceinline__ void lds2(const __half* p, float& a, float& b) {
         unpack(*reinterpret_cast<const unsigned int*>(p), a, b);
+    }
+    // the pair word as (A, B)
+    static __device__ __forceinline__ float2 unpack2(unsigned int w) {
+        return __half22float2(*reinterpret_cast<const __half2*>(&w));
+    }
+    static __device__ __forceinline__ float2 lds2v(const __half* p) {
+        return unpack2(*reinterpret_cast<const unsigned int*>(p));
     }
     static __device__ __forceinline__ void st2(__half* p, float a, float b) {
         const __half2 h = __floats2half2_rn(a, b);
@@ -95,6 +104,13 @@ template <> struct Store<__nv_bfloat16> {
     }
     static __device__ __forceinline__ void lds2(const __nv_bfloat16* p, float& a, float& b) {
         unpack(*reinterpret_cast<const unsigned int*>(p), a, b);
+    }
+    // the pair word as (A, B)
+    static __device__ __forceinline__ float2 unpack2(unsigned int w) {
+        return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+    }
+    static __device__ __forceinline__ float2 lds2v(const __nv_bfloat16* p) {
+        return unpack2(*reinterpret_cast<const unsigned int*>(p));
     }
     static __device__ __forceinline__ void st2(__nv_bfloat16* p, float a, float b) {
         const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);

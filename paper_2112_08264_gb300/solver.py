@@ -26,6 +26,15 @@ def _ptr(t, n, what, optional=False):
     return t.data_ptr()
 
 
+class _DeviceSpan:
+    """Bytes of device memory owned by the library's workspace, exposed through
+    the CUDA array interface so that torch can alias them without a copy."""
+
+    def __init__(self, ptr, nbytes, device):
+        self.__cuda_array_interface__ = {"shape": (int(nbytes),), "typestr": "|u1", "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
+
+
 class Solver:
     """Two-component D3Q19 BGK Shan-Chen lattice-Boltzmann solver on one GPU.
 
@@ -42,7 +51,7 @@ class Solver:
 
     def __init__(self, nx, ny, nz, tau, G, mask=None, prec="fp32", kernel="fused", rho0=(0.0, 0.0),
                  body_force=(0.0, 0.0, 0.0), ckpt_every=0, ckpt_steps_max=0, device=None, stream=None,
-                 model="shan_chen", cg=None, max_particles=0):
+                 model="shan_chen", cg=None, max_particles=0, slab_halo=0):
         L = _lib.lib()
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.shape = (self.nz, self.ny, self.nx)
@@ -51,7 +60,7 @@ class Solver:
         self.prec, self.kernel = prec, kernel
         self.model = model
         self.opt = _lib.options(prec, kernel, rho0, body_force, ckpt_every, ckpt_steps_max, model, cg,
-                                max_particles)
+                                max_particles, slab_halo)
         self.n_particles = 0
         nbytes = _lib.workspace_bytes(self.nx, self.ny, self.nz, self.opt)
         if nbytes == 0:
@@ -116,6 +125,32 @@ class Solver:
         """FP64 [mass_A, mass_B, Px, Py, Pz] (synchronous)."""
         out = (ctypes.c_double * 5)()
         _lib.check(_lib.lib().lb_stats(self._h, out), "lb_stats")
+        return np.array(out[:], dtype=np.float64)
+
+    # -- one rank's slab of a decomposed lattice (slab_halo > 0) -------------
+    def step_fluid(self):
+        """The step kernel of one step, without the bounce-back pass (``lb_step_fluid``)."""
+        _lib.check(_lib.lib().lb_step_fluid(self._h), "lb_step_fluid")
+
+    def step_links(self):
+        """The write-side bounce-back pass that completes the step (``lb_step_links``)."""
+        _lib.check(_lib.lib().lb_step_links(self._h), "lb_step_links")
+
+    def planes(self):
+        """The current state as a (nz, bytes per plane) uint8 device tensor that
+        aliases the library's storage (``lb_planes``; valid until the next
+        step): plane z is row z, in the library's internal format, for
+        copying border planes between ranks."""
+        ptr, nbytes = ctypes.c_void_p(), ctypes.c_size_t()
+        _lib.check(_lib.lib().lb_planes(self._h, 0, self.nz, ctypes.byref(ptr), ctypes.byref(nbytes)),
+                   "lb_planes")
+        span = _DeviceSpan(ptr.value, nbytes.value, self.device)
+        return torch.as_tensor(span, device=self.device).view(self.nz, nbytes.value // self.nz)
+
+    def stats_planes(self, z0, nplanes):
+        """FP64 [mass_A, mass_B, Px, Py, Pz] over planes [z0, z0 + nplanes)."""
+        out = (ctypes.c_double * 5)()
+        _lib.check(_lib.lib().lb_stats_planes(self._h, int(z0), int(nplanes), out), "lb_stats_planes")
         return np.array(out[:], dtype=np.float64)
 
     def get_state(self, out=None):

@@ -3,7 +3,7 @@
 
 Tolerances as for the Shan-Chen path: element-wise states within a few FP32
 ulps of the largest population after one step; densities within 1e-5
-(max-relative) after 50 steps in FP32, 2e-3 with FP16 and 4e-3 with BF16
+(max-relative) after 50 steps in FP32, 2e-3 with FP16 and BF16
 storage; the box
 kernel and the two-pass kernels give the same bits; per-component mass and
 total momentum conserved step by step (FP64 totals).
@@ -84,9 +84,10 @@ def test_box_and_two_pass_are_bitwise_equal(prec):
     b.close()
 
 
-# BF16 (8 mantissa bits) on colour-gradient deviations, which reach half of
-# w_i rho in segregated phases: 4e-3 (measured 2.1e-3 after 50 steps)
-@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("fp16", 2e-3), ("bf16", 4e-3)])
+# The 16-bit bar is 2e-3 for both types. BF16 (8 mantissa bits) on
+# colour-gradient deviations, which reach half of w_i rho in segregated
+# phases, measured 1.5e-3 (rho_A) and 1.3e-3 (rho_B) after 50 steps.
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("fp16", 2e-3), ("bf16", 2e-3)])
 def test_moments_50_steps_and_conservation(prec, tol):
     shape = (32, 32, 16)
     rA, rB, u = fields(shape, 3)
@@ -103,8 +104,10 @@ def test_moments_50_steps_and_conservation(prec, tol):
     gA, gB, gu = (x.cpu().numpy().astype(np.float64) for x in s.moments())
     s.close()
     oA, oB, ou = cg.moments(oracle_cg(50, rA, rB, u))
-    for a, b in ((gA, oA), (gB, oB)):
-        assert np.abs(a - b).max() / np.abs(b).max() <= tol
+    errs = [np.abs(a - b).max() / np.abs(b).max() for a, b in ((gA, oA), (gB, oB))]
+    print("\ncolour gradient %s, 50 steps: rho_A %.3e rho_B %.3e" % (prec, errs[0], errs[1]))
+    for e in errs:
+        assert e <= tol
     if prec == "fp32":
         assert np.abs(gu - ou).max() <= 1e-4 * np.sqrt((ou * ou).sum(axis=0)).max()
 
@@ -138,7 +141,7 @@ def test_rejected_configurations():
         Solver(16, 16, 16, 1.0, 0.0, model="colour_gradient", cg=CG, ckpt_every=4, ckpt_steps_max=8)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+@pytest.mark.parametrize("prec", ["fp32", "fp16", "bf16"])
 def test_full_size_256_tiled_state(prec):
     """256^3 in the benchmark's launch configuration (the box kernel, one
     launch per step): a random 16^3 periodic state tiled 16 times per axis
@@ -154,6 +157,38 @@ def test_full_size_256_tiled_state(prec):
     got = s.get_state()
     want = ln.to_public(oracle_cg(steps, rA, rB, u))
     want_t = torch.tensor(want.astype(np.float32), device="cuda").repeat(1, 1, *reps)
-    tol = {"fp32": 4e-7, "fp16": 5e-4}[prec] * float(want_t.abs().max())
+    # BF16: the FP16 bound times the ratio of the half-ulps (2^-8 / 2^-11 = 8)
+    tol = {"fp32": 4e-7, "fp16": 5e-4, "bf16": 4e-3}[prec] * float(want_t.abs().max())
     assert float((got - want_t).abs().max()) <= tol
     s.close()
+
+
+@pytest.mark.parametrize("gmax", [1.2e-5, 0.8e-5])
+def test_gradient_threshold_matches_oracle(gmax):
+    """Where |grad Theta| <= 1e-5 both sides switch the perturbation and the
+    recolouring off. A near-pure phase rho^A = 1 - eps(y), rho^B = eps(y), eps
+    a sine on 8 rows, has |grad Theta| = gmax |cos(2 pi y / 8)|: with gmax =
+    1.2e-5 the rows at 1.2e-5 are above the threshold and those at 0.85e-5 and
+    0 below (margins far beyond the FP32 rounding of the gradient, about 0.5 %
+    here); with 0.8e-5 every row is below. One step matches the oracle element
+    by element in both cases (a switched-on recolouring there moves
+    populations by about 4e-5, far above the tolerance)."""
+    n = 8
+    y = np.arange(n)
+    prof = np.broadcast_to(np.sin(2 * np.pi * y / n)[None, :, None], (n, n, n))
+    # discrete gradient of a function of y: (Theta(y + 1) - Theta(y - 1)) / 2
+    amp = gmax / (2.0 * np.sin(2 * np.pi / n))   # eps amplitude (Theta = 1 - 2 eps)
+    eps = np.float32(1e-3 + amp * prof).astype(np.float64)
+    rA = np.float32(1.0 - eps).astype(np.float64)
+    rB = eps
+    _, grad = cg.phase_gradient(rA, rB)
+    gn = np.sqrt((grad * grad).sum(axis=0))
+    assert abs(gn.max() - gmax) <= 0.01 * gmax
+    if gmax > 1e-5:
+        assert (gn > 1.1e-5).any() and (gn < 0.9e-5).any()
+    s = gpu_cg((n, n, n), 1, rA, rB)
+    got = s.get_state().cpu().numpy().astype(np.float64)
+    s.close()
+    want = ln.to_public(oracle_cg(1, rA, rB))
+    err = np.abs(got - want).max() / np.abs(want).max()
+    assert err < 8 * 2.0 ** -24 * 4, err

@@ -64,3 +64,43 @@ def test_precision_against_oracle_64cubed_500_steps(reference, prec):
     assert out["rho_A"][0] <= TOL[prec] and out["rho_B"][0] <= TOL[prec]
     floor = 8 * HALF_ULP[prec] * R["dmax"] / min(R["oA"].min() + R["oB"].min(), 1.0)
     assert np.abs(du).max() <= max(TOL[prec] * uscale, floor)
+
+
+# A flow-dominated two-component case: the decaying shear wave
+# u_x = 1e-3 sin(2 pi y / ny) through the seeded spinodal mixture (40 x 32 x 24,
+# tau = 0.8, G = 0.65, seed 55), 100 steps. rho_A, rho_B and u (as a vector
+# field) are held to the plain 2e-3 max-relative bar with no storage floor.
+# BF16 keeps 8 significant bits: every stored deviation (about w_i * 0.05 from
+# the density noise, against about w_i * 1.5e-3 from the flow) is rounded to
+# 2^-9 of itself, and the velocity, a difference of such values, comes out
+# at 6.6e-3 of max|u| in an FP64 emulation of the rounding; FP16 (11 bits)
+# gives 1.0e-3 there. The BF16 velocity therefore
+# misses the bar, which stays 2e-3: the case is an expected failure.
+@pytest.mark.parametrize("prec", [
+    "fp16",
+    pytest.param("bf16", marks=pytest.mark.xfail(
+        strict=True, reason="BF16 storage resolves this flow's velocity to about 6e-3 of max|u| (bar 2e-3)")),
+])
+def test_flow_dominated_reduced_precision_100_steps(prec):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    nx, ny, nz, tau, G, steps = 40, 32, 24, 0.8, 0.65, 100
+    rA, rB = inputs.spinodal(nx, ny, nz, seed=55)
+    u = np.zeros((3, nz, ny, nx))
+    u[0] = 1e-3 * np.sin(2 * np.pi * np.arange(ny) / ny)[None, :, None]
+    dev = lambda a: torch.tensor(np.asarray(a, np.float32), device="cuda")
+    s = Solver(nx, ny, nz, tau, G, prec=prec)
+    s.init(dev(rA), dev(rB), dev(u))
+    s.step(steps)
+    gA, gB, gu = (t.cpu().numpy().astype(np.float64) for t in s.moments())
+    s.close()
+    r32 = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    f = oracle.run(oracle.init(r32(rA), r32(rB), r32(u)), steps, tau, G)
+    oA, oB, ou = oracle.moments(f, G)
+    eA = np.abs(gA - oA).max() / np.abs(oA).max()
+    eB = np.abs(gB - oB).max() / np.abs(oB).max()
+    eu = np.abs(gu - ou).max() / np.sqrt((ou * ou).sum(axis=0)).max()
+    print("\nflow-dominated %s: rho_A %.3e rho_B %.3e u %.3e" % (prec, eA, eB, eu))
+    assert eA <= TOL[prec] and eB <= TOL[prec]
+    assert eu <= TOL[prec]

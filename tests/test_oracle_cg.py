@@ -115,3 +115,40 @@ def test_laplace_law():
         dp = ln.CS2 * (rho[r < R - 3].mean() - rho[r > R + 3].mean())
         out.append(dp * R / (2 * sigma))
     assert all(abs(v - 1.0) < 0.1 for v in out), out   # measured 1.04 and 1.00
+
+
+@pytest.mark.parametrize("gmax,active", [(1.2e-5, True), (0.8e-5, False)])
+def test_gradient_threshold_decides(gmax, active):
+    """The perturbation and the recolouring act only where |grad Theta| >
+    GRAD_MIN = 1e-5 (the reading for a vanishing gradient, whose direction is
+    undefined). A near-pure phase rho^A = 1 - eps(y), rho^B = eps(y) with a
+    sine eps scaled so that max |grad Theta| is 1.2e-5 (above) or 0.8e-5
+    (below): above, the collision differs from plain BGK (sigma = beta = 0)
+    exactly at the nodes whose gradient passes the threshold; below, it is
+    plain BGK at every node. A threshold on |grad Theta|^2, or none at all,
+    fails one of the two cases."""
+    n = 12
+    y = np.arange(n)
+    shape = np.broadcast_to(np.sin(2 * np.pi * y / n)[None, :, None], (n, n, n))
+    # Theta = 1 - 2 eps at rho = 1, so grad Theta is linear in the amplitude
+    eps0 = 1e-3 + 1e-4 * shape
+    _, g0 = cg.phase_gradient(1.0 - eps0, eps0)
+    g0n = np.sqrt((g0 * g0).sum(axis=0))
+    amp = 1e-4 * gmax / g0n.max()
+    eps = 1e-3 + amp * shape
+    rA, rB = 1.0 - eps, eps
+    _, grad = cg.phase_gradient(rA, rB)
+    gn = np.sqrt((grad * grad).sum(axis=0))
+    assert abs(gn.max() - gmax) <= 1e-3 * gmax
+    f = ln.init(rA, rB, np.zeros((3, n, n, n)))
+    nu = 1.0 / 6.0
+    full = cg.collide(f, nu, nu, 0.01, 0.7)
+    plain = cg.collide(f, nu, nu, 0.0, 0.0)
+    diff = np.abs(full - plain).max(axis=(0, 1))
+    if active:
+        over = gn > cg.GRAD_MIN
+        assert over.any() and (~over).any()
+        assert np.all(diff[over] > 1e-12)
+        assert np.all(diff[~over] == 0.0)
+    else:
+        assert np.all(diff == 0.0)

@@ -5,7 +5,8 @@ allocator of any library), and so cannot hand lb_create a workspace: they
 pass a population field and output buffers they already own, and the entry
 point keeps its neighbour-density scratch in a static device array. These
 checks call it through the C ABI and compare its output with lb_moments on
-the same state, within the parity tolerances of the other GPU tests (1e-5
+the same state and with the FP64 oracle's moments of the same population
+field, within the parity tolerances of the other GPU tests (1e-5
 max-relative on densities, 1e-5 of max|u| on the velocity of a flowing case),
 on two calls in a row with different grids and states. This file sorts last
 so that a run stopping at the first failure has run every other test.
@@ -70,6 +71,13 @@ def test_noalloc_moments_match_lb_moments_on_two_calls():
         uerr = float((ou - refu).abs().max())
         uscale = float(refu.pow(2).sum(dim=0).sqrt().max())
         assert uerr <= 1e-5 * uscale
+        # the FP64 oracle's moments of the same (FP32) population field
+        import oracle
+        wA, wB, wu = oracle.moments(f.cpu().numpy().astype(np.float64), G, g, mask)
+        for got, want in ((oA, wA), (oB, wB)):
+            assert np.abs(got.cpu().numpy() - want).max() <= 1e-5 * np.abs(want).max()
+        wscale = np.sqrt((wu * wu).sum(axis=0)).max()
+        assert np.abs(ou.cpu().numpy() - wu).max() <= 1e-5 * wscale
         if mask is not None:
             m = torch.tensor(mask == 1, device="cuda")
             assert float(oA[m].abs().max()) == 0.0 and float(ou[:, m].abs().max()) == 0.0
