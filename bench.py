@@ -158,11 +158,14 @@ def workload(name, grid=None):
         return dict(shape=(n, n, n), tau=1.0, G=0.65, rA=rA, rB=rB, mask=None, traffic="" if n == 256 else None,
                     desc="spinodal %d^3 periodic, tau=1, G=0.65, rho_A=0.5+0.05U(-1,1) seed 1234" % n)
     if name == "colloid256":
-        n = 256
+        # the grid override keeps the solid fraction: 4000 spheres per 256^3 (profiling cases)
+        n = grid or 256
+        count = max(1, int(round(4000 * (n / 256.0) ** 3)))
         rA, rB = inputs.spinodal(n, n, n, seed=1234)
-        mask, _ = inputs.colloid_mask(n, n, n, n_spheres=4000, radius=5.0, seed=4321)
-        return dict(shape=(n, n, n), tau=1.0, G=0.65, rA=rA, rB=rB, mask=mask, traffic="colloid_",
-                    desc="256^3, 4000 static spheres R=5 (seed 4321), halfway bounce-back")
+        mask, _ = inputs.colloid_mask(n, n, n, n_spheres=count, radius=5.0, seed=4321)
+        return dict(shape=(n, n, n), tau=1.0, G=0.65, rA=rA, rB=rB, mask=mask,
+                    traffic="colloid_" if n == 256 else None,
+                    desc="%d^3, %d static spheres R=5 (seed 4321), halfway bounce-back" % (n, count))
     if name == "orderparam256":
         n = grid or 256
         rA, rB = inputs.random_order_parameter(n, n, n, seed=1234)

@@ -179,21 +179,40 @@ __global__ void __launch_bounds__(kPT) sphere_links_kernel(S* __restrict__ st, c
         const int ym = wrap_dec(x[1], g.ny), yp = wrap_inc(x[1], g.ny);
         const int zm = wrap_dec(x[2], g.nz), zp = wrap_inc(x[2], g.nz);
         const int h0[3] = {2 * (u[0] - cube.base[0]), 2 * (u[1] - cube.base[1]), 2 * (u[2] - cube.base[2])};
+        auto target = [&](auto I) -> uint32_t {   // site x + c_i
+            constexpr int i = decltype(I)::value;
+            constexpr int cx = Vel<i>::x, cy = Vel<i>::y, cz = Vel<i>::z;
+            const int t3[3] = {cx > 0 ? xp : (cx < 0 ? xm : x[0]), cy > 0 ? yp : (cy < 0 ? ym : x[1]),
+                               cz > 0 ? zp : (cz < 0 ? zm : x[2])};
+            return site_of(t3, g);
+        };
+        // The node's links to this sphere, then their populations, each as a
+        // batch of independent loads (the owner and population of one link
+        // are a chain of two DRAM round trips; batched, the node's links
+        // overlap theirs), then the slots and the force.
+        uint32_t lmask = 0;
+        static_for<1, Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            if (fl & (1u << Vel<i>::opp))   // x + c_i is solid: is it this sphere?
+                if (__ldg(A.owner + target(I)) == q + 1) lmask |= 1u << i;
+        });
+        float pA[Q], pB[Q];
+        static_for<1, Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            pA[i] = pB[i] = 0.f;
+            if (lmask & (1u << i)) Store<S>::ld2(st + pidx(0, i, s), pA[i], pB[i]);
+        });
         static_for<1, Q>([&](auto I) {
             constexpr int i = decltype(I)::value;
             constexpr int cx = Vel<i>::x, cy = Vel<i>::y, cz = Vel<i>::z;
             constexpr int w36 = Vel<i>::c2 == 1 ? 2 : 1;
-            if (!(fl & (1u << Vel<i>::opp))) return;   // x + c_i is fluid
-            const int t3[3] = {cx > 0 ? xp : (cx < 0 ? xm : x[0]), cy > 0 ? yp : (cy < 0 ? ym : x[1]),
-                               cz > 0 ? zp : (cz < 0 ? zm : x[2])};
-            const uint32_t t = site_of(t3, g);
-            if (A.owner[t] != q + 1) return;
+            if (!(lmask & (1u << i))) return;
+            const uint32_t t = target(I);
             const float arm[3] = {d[0] + 0.5f * cx, d[1] + 0.5f * cy, d[2] + 0.5f * cz};
             float wa[3];
             cross(w, arm, wa);
             const float cu = 3.0f * (cx * (v[0] + wa[0]) + cy * (v[1] + wa[1]) + cz * (v[2] + wa[2]));
-            float dA, dB;
-            Store<S>::ld2(st + pidx(0, i, s), dA, dB);
+            const float dA = pA[i], dB = pB[i];
             const float bA = 2.0f * p.rho0[0] * wgt<i>() * cu;
             const float bB = 2.0f * p.rho0[1] * wgt<i>() * cu;
             Store<S>::st2(st + pidx(0, Vel<i>::opp, t), dA - bA, dB - bB);
