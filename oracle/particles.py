@@ -48,12 +48,15 @@ Readings where the paper is silent (listed with the design notes):
 * the lubrication force is named with its range (2/3 of a lattice unit)
   but not given: the normal lubrication correction above is the reading.
 
-State (the library's write-side representation): g holds the post-collision
-populations at fluid nodes and, at solid nodes, the slots the next pull
-reads (slot opp(i) of solid y = x + c_i holds the bounced population of
-fluid x). Arrays use ``lb_numpy``'s velocity order (``VEL``), shape
-(2, 19, nz, ny, nx); ``post_streaming`` gives the pulled populations in that
-order.
+Two formulations of the same step. ``step`` keeps the library's write-side
+representation: g holds the post-collision populations at fluid nodes and,
+at solid nodes, the slots the next pull reads (slot opp(i) of solid
+y = x + c_i holds the bounced population of fluid x); ``pulled`` gives the
+post-streaming populations it stands for. ``step_pull`` keeps the C oracle's
+post-streaming representation (nothing stored on solid nodes) and applies the
+moving-wall bounce-back while streaming. They are written apart and pinned
+against each other; the GPU is checked against ``step_pull``. Arrays use
+``lb_numpy``'s velocity order (``VEL``), shape (2, 19, nz, ny, nx).
 """
 import numpy as np
 
@@ -329,6 +332,105 @@ def step(g, owner, mask, parts, tau, G, rho0, gbody=None):
     advance(parts, (nx, ny, nz), (rho0[0] + rho0[1]) * (tau - 0.5) / 3.0)
     gnew, owner = remesh(gnew, owner, mask, parts, rho0)
     return gnew, owner
+
+
+# ---------------------------------------------------------------------------
+# The same step in the post-streaming representation of the C oracle: the
+# state is the pulled, pre-collision f at fluid nodes and nothing at solid
+# nodes; the moving-wall bounce-back of Eq. LADDFLBE is applied while
+# streaming (push form), where the exchanged momentum of Eq. FORCEPP is
+# summed. Written apart from the write-side form above (which stores the
+# bounced populations in slots of the solid nodes, as the library does) so
+# that the two can pin each other.
+#
+# Order: a step's force comes from the streaming that made its state, with
+# the sphere velocities of that moment; then collision, leap-frog with that
+# force, re-meshing of the post-collision field, and the streaming that makes
+# the next state and the next step's force. parts.F, parts.T after a step are
+# the force and torque that step's leap-frog used.
+
+
+def stream(g, owner, mask, parts, rho0):
+    """Push the post-collision g of the fluid nodes along c_i: into the
+    neighbour when it is fluid, back into population opp(i) of the same node
+    when it is solid -- at rest for a static solid, reduced by
+    2 rho0^k w_i (u_b . c_i) / c_s^2 for a node covered by a sphere moving with
+    u_b = v + w x (r_b - r) at the link midpoint r_b. Returns (f, F, T), F and
+    T the momentum and its moment each sphere takes from its links."""
+    shape = g.shape[2:]
+    nz, ny, nx = shape
+    solid = _solid(mask, owner)
+    fluid = ~solid
+    static = np.zeros(shape, bool) if mask is None else (np.asarray(mask) != 0)
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    P = len(parts.r)
+    F = np.zeros((P, 3))
+    T = np.zeros((P, 3))
+    f = np.zeros_like(g)
+    for i, c in enumerate(VEL):
+        o = OPP[i]
+        into_fluid = fluid & shift_from(fluid, c)          # x fluid, x + c_i fluid
+        for k in range(2):
+            f[k, i] += shift_to(np.where(into_fluid, g[k, i], 0.0), c)
+        if not c.any():
+            continue
+        back = fluid & shift_from(static, c)               # x + c_i a static solid
+        for k in range(2):
+            f[k, o] += np.where(back, g[k, i], 0.0)
+        nb_owner = shift_from(owner, c)
+        for p in range(P):
+            at = fluid & (nb_owner == p)
+            if not at.any():
+                continue
+            arm = _arm(shape, x[at] + 0.5 * c[0], y[at] + 0.5 * c[1], z[at] + 0.5 * c[2], parts.r[p])
+            ub = parts.v[p][:, None] + np.cross(parts.w[p], arm.T).T
+            cu = (c[:, None] * ub).sum(axis=0) / CS2
+            exch = np.zeros(arm.shape[1])
+            for k in range(2):
+                gi = g[k, i][at]
+                bias = 2.0 * rho0[k] * W[i] * cu
+                f[k, o][at] += gi - bias
+                exch += 2.0 * gi - bias
+            dF = c[:, None] * exch[None, :]
+            F[p] += dF.sum(axis=1)
+            T[p] += np.cross(arm.T, dF.T).sum(axis=0)
+    return f, F, T
+
+
+def unstream(f, solid):
+    """The post-collision field whose streaming with bounce-back at rest gives
+    f back: g_i(y) = f_i(y + c_i) where y + c_i is fluid, f_opp(i)(y) where it
+    is solid; 0 on solid nodes."""
+    fluid = ~solid
+    g = np.zeros_like(f)
+    for i, c in enumerate(VEL):
+        ahead_fluid = shift_from(fluid, c)
+        for k in range(2):
+            g[k, i] = np.where(fluid & ahead_fluid, shift_from(f[k, i], c), 0.0)
+            g[k, i] += np.where(fluid & ~ahead_fluid, f[k, OPP[i]], 0.0)
+    return g
+
+
+def init_pull(rhoA, rhoB, u, mask, owner, parts, rho0):
+    """Initial post-streaming state: the equilibrium f^eq(rho^k, u) at fluid
+    nodes, streamed once more from the field that reproduces it at rest, so
+    that nodes next to a moving sphere see its wall (the first step's force
+    is set in parts.F_next, parts.T_next)."""
+    solid = _solid(mask, owner)
+    feq = ln.init(rhoA, rhoB, u, solid.astype(np.uint8))
+    f, parts.F_next, parts.T_next = stream(unstream(feq, solid), owner, mask, parts, rho0)
+    return f
+
+
+def step_pull(f, owner, mask, parts, tau, G, rho0, gbody=None):
+    """One step in the post-streaming representation; returns (f, owner)."""
+    parts.F, parts.T = parts.F_next, parts.T_next
+    g = collide(f, tau, G, gbody, _solid(mask, owner))
+    nz, ny, nx = f.shape[2:]
+    advance(parts, (nx, ny, nz), (rho0[0] + rho0[1]) * (tau - 0.5) / 3.0)
+    g, owner = remesh(g, owner, mask, parts, rho0)
+    f, parts.F_next, parts.T_next = stream(g, owner, mask, parts, rho0)
+    return f, owner
 
 
 def fluid_momentum(g, owner, mask):

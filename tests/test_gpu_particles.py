@@ -1,5 +1,7 @@
 """Moving rigid spheres on the GPU (``lb_particles_set`` / ``lb_step``)
-against the FP64 particle oracle (``oracle.particles``), through the C ABI.
+against the FP64 particle oracle (``oracle.particles``, its post-streaming
+formulation ``init_pull`` / ``step_pull``: the C oracle's representation, no
+populations stored on solid nodes), through the C ABI.
 
 Bars: fixed spheres at rest give, bit for bit, the state of the static mask
 they cover (their slots carry no bias); moving spheres follow the oracle
@@ -61,8 +63,8 @@ def oracle_init(shape, spheres, rA, rB, u, mask=None):
     owner = op.coverage((nz, ny, nx), parts.r, parts.radius)
     fluid = (owner < 0) if mask is None else (owner < 0) & (mask == 0)
     rho0 = (rA[fluid].mean(), rB[fluid].mean())
-    g = op.init(rA, rB, u, mask, owner)
-    return g, owner, parts, rho0
+    f = op.init_pull(rA, rB, u, mask, owner, parts, rho0)
+    return f, owner, parts, rho0
 
 
 TWO = dict(r=[[9.3, 8.4, 7.7], [23.6, 17.2, 12.9]], v=[[0.21, -0.12, 0.07], [-0.15, 0.08, 0.18]],
@@ -101,11 +103,11 @@ def test_moving_spheres_follow_the_oracle(prec):
     tau, G, steps = 0.9, 0.6, 8
     rA, rB, u = fields(shape, 2)
     s = gpu_run(shape, TWO, 0, tau, G, rA, rB, u, prec=prec)
-    g, owner, parts, rho0 = oracle_init(shape, TWO, rA, rB, u)
+    f, owner, parts, rho0 = oracle_init(shape, TWO, rA, rB, u)
     owner0 = owner.copy()
     for t in range(steps):
         s.step(1)
-        g, owner = op.step(g, owner, None, parts, tau, G, rho0)
+        f, owner = op.step_pull(f, owner, None, parts, tau, G, rho0)
         p = s.particles()
         for k, ref in (("r", parts.r), ("v", parts.v), ("w", parts.w), ("F", parts.F), ("T", parts.T)):
             if bars[k] is None:
@@ -114,7 +116,7 @@ def test_moving_spheres_follow_the_oracle(prec):
             assert np.abs(p[k] - ref).max() <= bar, (t, k, p[k], ref)
     assert (owner != owner0).sum() > 20            # re-meshing happened
     got = s.get_state().cpu().numpy().astype(np.float64)
-    want = ln.to_public(op.pulled(g, owner, None, parts, rho0))
+    want = ln.to_public(f)
     assert np.abs(got - want).max() <= bars["state"] * np.abs(want).max()
 
 
@@ -180,11 +182,11 @@ def test_full_size_256_tiled_moving_spheres():
     big = lambda a: torch.tensor(np.asarray(a, np.float32), device="cuda").repeat(reps, reps, reps).contiguous()
     s.init(big(rA), big(rB), torch.stack([big(u[a]) for a in range(3)]).contiguous())
     s.step(steps)
-    g, owner, parts, rho0 = oracle_init((p, p, p), one, rA, rB, u)
+    f, owner, parts, rho0 = oracle_init((p, p, p), one, rA, rB, u)
     for _ in range(steps):
-        g, owner = op.step(g, owner, None, parts, tau, G, rho0)
+        f, owner = op.step_pull(f, owner, None, parts, tau, G, rho0)
     got = s.get_state()
-    want = ln.to_public(op.pulled(g, owner, None, parts, rho0))
+    want = ln.to_public(f)
     want_t = torch.tensor(want.astype(np.float32), device="cuda").repeat(1, 1, reps, reps, reps)
     assert float((got - want_t).abs().max()) <= 8e-7 * float(want_t.abs().max())
     q = s.particles()
@@ -207,11 +209,11 @@ def test_contact_force_turns_spheres_back_as_the_oracle():
     s.init(dev(rA), dev(rB), dev(u))
     parts = op.Particles(sph["r"], sph["v"], None, sph["radius"], sph["mass"], contact=(0.5, 1.5))
     owner = op.coverage((nz, ny, nx), parts.r, parts.radius)
-    g = op.init(rA, rB, u, None, owner)
+    f = op.init_pull(rA, rB, u, None, owner, parts, rho0)
     turned = False
     for _ in range(70):
         s.step(1)
-        g, owner = op.step(g, owner, None, parts, 1.0, 0.0, rho0)
+        f, owner = op.step_pull(f, owner, None, parts, 1.0, 0.0, rho0)
         p = s.particles()
         assert np.abs(p["r"] - parts.r).max() <= 1e-5
         assert np.abs(p["v"] - parts.v).max() <= 1e-5 * 0.06       # of the initial speed
@@ -233,16 +235,16 @@ def test_moving_spheres_between_static_walls(prec):
                w=[[0.0, 0.01, -0.02], [0.015, 0.0, 0.01]], radius=3.2, mass=60.0)
     rA, rB, u = fields(shape, 6)
     s = gpu_run(shape, sph, 0, 0.9, 0.6, rA, rB, u, prec=prec, mask=mask)
-    g, owner, parts, rho0 = oracle_init(shape, sph, rA, rB, u, mask)
+    f, owner, parts, rho0 = oracle_init(shape, sph, rA, rB, u, mask)
     for _ in range(6):
         s.step(1)
-        g, owner = op.step(g, owner, mask, parts, 0.9, 0.6, rho0)
+        f, owner = op.step_pull(f, owner, mask, parts, 0.9, 0.6, rho0)
     p = s.particles()
     bars = BARS[prec]
     assert np.abs(p["r"] - parts.r).max() <= bars["r"]
     assert np.abs(p["v"] - parts.v).max() <= bars["v"] * np.abs(parts.v).max()
     got = s.get_state().cpu().numpy().astype(np.float64)
-    want = ln.to_public(op.pulled(g, owner, mask, parts, rho0))
+    want = ln.to_public(f)
     assert np.abs(got - want).max() <= bars["state"] * np.abs(want).max()
 
 
@@ -335,10 +337,10 @@ def test_lubrication_as_the_oracle():
     s.init(dev(rA), dev(rB), dev(u))
     parts = op.Particles(sph["r"], sph["v"], None, sph["radius"], sph["mass"], lubrication=2.0 / 3.0)
     owner = op.coverage((nz, ny, nx), parts.r, parts.radius)
-    g = op.init(rA, rB, u, None, owner)
+    f = op.init_pull(rA, rB, u, None, owner, parts, rho0)
     for _ in range(8):
         s.step(1)
-        g, owner = op.step(g, owner, None, parts, 1.0, 0.0, rho0)
+        f, owner = op.step_pull(f, owner, None, parts, 1.0, 0.0, rho0)
         p = s.particles()
         assert np.abs(p["r"] - parts.r).max() <= 1e-6
         assert np.abs(p["v"] - parts.v).max() <= 1e-4 * 0.004
