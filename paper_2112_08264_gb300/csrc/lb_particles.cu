@@ -111,6 +111,49 @@ __device__ __forceinline__ uint32_t site_of(const int (&x)[3], const Geom& g) {
     return (uint32_t)x[0] + (uint32_t)g.nx * ((uint32_t)x[1] + (uint32_t)g.ny * (uint32_t)x[2]);
 }
 
+// This thread's nodes of a sphere's cube (b = threadIdx.x + k kPT), eight at a
+// time: cand(u, x, r2) picks the nodes to visit (it is called for every node),
+// the owner of every picked node of the batch is loaded first -- independent
+// loads whose DRAM round trips overlap, where one load per node in turn
+// would wait for each -- and then body(u, x, r2, owner) runs for each.
+// Another block writes an owner only for its own sphere's nodes, so a value
+// read here either is this sphere's mark or says the node is not this
+// sphere's.
+template <typename Cand, typename Body>
+__device__ __forceinline__ void cube_batches(const Cube& cube, const Geom& g, const int* owner, Cand&& cand,
+                                             Body&& body) {
+    constexpr int kB = 8;
+    for (int b0 = threadIdx.x; b0 < cube.count(); b0 += kB * kPT) {
+        int own[kB];
+        bool ok[kB];
+#pragma unroll
+        for (int k = 0; k < kB; ++k) {
+            const int b = b0 + k * kPT;
+            ok[k] = false;
+            own[k] = 0;
+            if (b < cube.count()) {
+                int u[3], x[3];
+                cube.at(b, g, u, x);
+                float df[3];
+                const float r2 = cube.dist2(u, df);
+                if (cand(u, x, r2)) {
+                    ok[k] = true;
+                    own[k] = __ldg(owner + site_of(x, g));
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kB; ++k) {
+            if (!ok[k]) continue;
+            int u[3], x[3];
+            cube.at(b0 + k * kPT, g, u, x);
+            float df[3];
+            const float r2 = cube.dist2(u, df);
+            body(u, x, r2, own[k]);
+        }
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void cross(const T (&a)[3], const T (&b)[3], T (&o)[3]) {
     o[0] = a[1] * b[2] - a[2] * b[1];
@@ -353,15 +396,12 @@ __global__ void __launch_bounds__(kPT) sphere_uncover_kernel(S* __restrict__ st,
     if (within_margin(A, q, g)) return;   // the whole block: no node changed
     __syncthreads();
     double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int b = threadIdx.x; b < cube.count(); b += kPT) {
-        int u[3], x[3];
-        cube.at(b, g, u, x);
-        float df[3];
-        const float r2 = cube.dist2(u, df);
-        if (A.radius > 2.0 && r2 < in2) continue;   // deep inside: still covered
+    // deep inside (beyond R - 2): still covered
+    auto cand = [&](const int (&)[3], const int (&)[3], float r2) { return !(A.radius > 2.0 && r2 < in2); };
+    cube_batches(cube, g, A.owner, cand, [&](const int (&u)[3], const int (&x)[3], float r2, int own) {
+        if (own != q + 1) return;
+        if (covered(u, x, r2, c, R2, g)) return;
         const uint32_t s = site_of(x, g);
-        if (A.owner[s] != q + 1) continue;
-        if (covered(u, x, r2, c, R2, g)) continue;
         A.owner[s] = 0;
         A.moved[q] = 1;
         const double arm[3] = {disp(x[0], u[0], c[0], g.nx), disp(x[1], u[1], c[1], g.ny),
@@ -385,7 +425,7 @@ __global__ void __launch_bounds__(kPT) sphere_uncover_kernel(S* __restrict__ st,
             acc[a] -= r0 * ub[a];
             acc[3 + a] -= r0 * L[a];
         }
-    }
+    });
     block_sum(acc);
     if (threadIdx.x == 0 && A.mass > 0.0)
 #pragma unroll
@@ -412,21 +452,19 @@ __global__ void __launch_bounds__(kPT) sphere_cover_kernel(S* __restrict__ st, c
     const float Rf = (float)A.radius;
     float margin = 1e30f;   // distance from the surface of the nearest node
     double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int b = threadIdx.x; b < cube.count(); b += kPT) {
-        int u[3], x[3];
-        cube.at(b, g, u, x);
-        float df[3];
-        const float r2 = cube.dist2(u, df);
+    auto cand = [&](const int (&u)[3], const int (&x)[3], float r2) {
         margin = fminf(margin, fabsf(sqrtf(r2) - Rf));
-        if (r2 < in2) continue;   // covered before the move too
-        if (!covered(u, x, r2, c, R2, g)) continue;
+        // covered now, and not already deep inside before the move
+        return !(r2 < in2) && covered(u, x, r2, c, R2, g);
+    };
+    cube_batches(cube, g, A.owner, cand, [&](const int (&u)[3], const int (&x)[3], float, int own) {
+        if (own == q + 1) return;   // covered before
         const uint32_t s = site_of(x, g);
-        if (A.owner[s] == q + 1) continue;   // covered before
         if ((mask && mask[s]) || atomicCAS(A.owner + s, 0, q + 1) != 0) {
             atomicOr(A.err, 1);
-            continue;
+            return;
         }
-        if (!absorb) continue;
+        if (!absorb) return;
         A.moved[q] = 1;
         double m[3] = {0, 0, 0};
         static_for<1, Q>([&](auto I) {
@@ -451,7 +489,7 @@ __global__ void __launch_bounds__(kPT) sphere_cover_kernel(S* __restrict__ st, c
             acc[a] += m[a];
             acc[3 + a] += L[a];
         }
-    }
+    });
     // the margin of this centre (nodes beyond the cube are farther than its
     // half-width, which exceeds R + 1)
     __shared__ float mred[kPT];
