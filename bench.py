@@ -9,8 +9,10 @@ kernel are timed beside it. GLUPS = nx*ny*nz / (1e9 * seconds per step)
 
 One JSON line on rank 0. ``--impl reference`` times the FP64 CPU oracle on
 the host cores instead (bounded sample of the same workload). With N > 1
-(torchrun) every rank runs an independent replica (the single lattice is not
-decomposed across GPUs), and value = all site updates / max-over-ranks time.
+(torchrun) every rank runs an independent replica by default, and value = all
+site updates / max-over-ranks time; ``--decompose`` instead cuts the one
+lattice into z-slabs over the ranks, which exchange their border planes every
+step (strong scaling).
 """
 import argparse
 import json
@@ -140,6 +142,75 @@ def max_over_ranks(x, world):
     t = torch.tensor([x], dtype=torch.float64, device="cuda" if on_gpu else "cpu")
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def main_decomposed(args, W, world, rank, local):
+    """One lattice cut into z-slabs over the ranks (strong scaling; the paper's
+    multi-GPU scheme, Sec. 4): each rank a context over its planes plus two
+    ghost planes per side, stepped with lb_step_fluid, the exchange of border
+    planes (decomp.exchange, point-to-point messages of the process group) and
+    lb_step_links. value = the whole lattice's site updates / the slowest
+    rank's timed region. With one rank the slab is the whole periodic lattice
+    and its borders wrap onto its own ghosts (the same code path)."""
+    import torch
+    from paper_2112_08264_gb300 import Solver, decomp
+    nx, ny, nz = W["shape"]
+    N = nx * ny * nz
+    idx = decomp.extended_planes(nz, world, rank)
+    z0, z1 = decomp.slab_bounds(nz, world, rank)
+    rho0 = (float(np.float32(W["rA"]).astype(np.float64).mean()), float(np.float32(W["rB"]).astype(np.float64).mean()))
+    s = Solver(nx, ny, len(idx), W["tau"], W["G"], prec=args.prec, rho0=rho0, slab_halo=decomp.HALO)
+    s.init(torch.tensor(np.ascontiguousarray(W["rA"][idx]), dtype=torch.float32, device="cuda"),
+           torch.tensor(np.ascontiguousarray(W["rB"][idx]), dtype=torch.float32, device="cuda"))
+
+    def one_step():
+        s.step_fluid()
+        decomp.exchange(s.planes(), 0, rank, world)
+        s.step_links()
+
+    decomp.exchange(s.planes(), 0, rank, world)
+    s.step_links()
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    barrier(world)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record()
+        for _ in range(args.steps):
+            one_step()
+        e1.record()
+        e1.synchronize()
+    barrier(world)
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
+    step_s = ms / 1e3 / args.steps
+    totals = decomp.allreduce_sum(s.stats_planes(decomp.HALO, z1 - z0)).numpy()
+    s.close()
+    glups = N / step_s / 1e9
+    peak, peak_kind = measured_peaks()
+    bps = BYTES_PER_SITE[args.prec]
+    line = {
+        "metric": W.get("metric", METRIC), "value": glups, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "strong",
+        "vs_baseline": None, "dtype": DTYPE_TAG[args.prec], "data": "synthetic",
+        "config": {"workload": W["desc"], "grid": [nx, ny, nz], "prec": args.prec, "kernel": "fused",
+                   "parallelism": "z-slabs x%d (two ghost planes per side, exchanged every step)" % world,
+                   "slab_planes": [z1 - z0, len(idx)]},
+        "roofline": {"bound": "hbm", "achieved": bps * N / step_s / 1e9 / world, "peak": peak, "unit": "GB/s",
+                     "frac": bps * N / step_s / 1e9 / world / peak, "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_site": bps,
+                     "timed": "per GPU: its share of the lattice's algorithmic bytes over the whole step "
+                              "(kernel, border exchange, bounce-back pass)", "traffic": None},
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+        "conserved_totals": [float(x) for x in totals],
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
 
 
 def replica_throughput(ms_local, steps, sites_per_replica, world):
@@ -842,6 +913,9 @@ def main():
     ap.add_argument("--no-variants", action="store_true", help="skip the FP16/BF16/two-pass lines")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--decompose", action="store_true",
+                    help="cut one lattice into z-slabs over the ranks (strong scaling) instead of running "
+                         "independent replicas")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -855,6 +929,10 @@ def main():
     if rank == 0 or world > 1:
         build.build()
     W = workload(args.config, args.grid)
+    if args.decompose:
+        if W.get("model") is not None or W["mask"] is not None:
+            raise SystemExit("--decompose runs the periodic Shan-Chen workloads")
+        return main_decomposed(args, W, world, rank, local)
     if W.get("model") == "single":
         return main_single(args, W, world, rank, local)
     if W.get("model") == "particles":

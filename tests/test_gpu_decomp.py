@@ -110,3 +110,35 @@ def test_split_step_order_is_enforced():
     with pytest.raises((ValueError, _lib.LbError)):   # a slab carries no spheres
         Solver(16, 8, 10, 1.0, 0.5, slab_halo=2, max_particles=4)
     s.close()
+
+
+def test_slabs_at_256_cubed_match_whole_lattice_bitwise():
+    """The benchmark's grid cut into two slabs of 128 planes (each stepped by
+    the box kernel in its own launch configuration): the owned planes equal
+    the whole-lattice run bit for bit after 3 steps."""
+    n, steps = 256, 3
+    rA, rB = inputs.spinodal(n, n, n, seed=1234)
+    rho0 = (float(np.float32(rA).astype(np.float64).mean()), float(np.float32(rB).astype(np.float64).mean()))
+    full = Solver(n, n, n, 1.0, 0.65, rho0=rho0)
+    full.init(dev(rA), dev(rB))
+    full.step(steps)
+    want = full.get_state()
+    full.close()
+    slabs = []
+    for r in range(2):
+        idx = decomp.extended_planes(n, 2, r)
+        s = Solver(n, n, len(idx), 1.0, 0.65, rho0=rho0, slab_halo=decomp.HALO)
+        s.init(dev(rA[idx]), dev(rB[idx]))
+        slabs.append(s)
+    exchange(slabs)
+    for _ in range(steps):
+        for s in slabs:
+            s.step_fluid()
+        exchange(slabs)
+        for s in slabs:
+            s.step_links()
+    for r, s in enumerate(slabs):
+        z0, z1 = decomp.slab_bounds(n, 2, r)
+        got = s.get_state()[:, :, decomp.HALO:decomp.HALO + z1 - z0]
+        assert torch.equal(got, want[:, :, z0:z1]), r
+        s.close()

@@ -73,8 +73,8 @@ def test_precision_against_oracle_64cubed_500_steps(reference, prec):
 # BF16 keeps 8 significant bits: every stored deviation (about w_i * 0.05 from
 # the density noise, against about w_i * 1.5e-3 from the flow) is rounded to
 # 2^-9 of itself, and the velocity, a difference of such values, comes out
-# at 6.6e-3 of max|u| in an FP64 emulation of the rounding; FP16 (11 bits)
-# gives 1.0e-3 there. The BF16 velocity therefore
+# at 6.6e-3 of max|u| in an FP64 emulation of the rounding and at 6.6e-3 on
+# the GPU; FP16 (11 bits) gives 8.9e-4 (GPU). The BF16 velocity therefore
 # misses the bar, which stays 2e-3: the case is an expected failure.
 @pytest.mark.parametrize("prec", [
     "fp16",
