@@ -51,7 +51,7 @@ class Solver:
 
     def __init__(self, nx, ny, nz, tau, G, mask=None, prec="fp32", kernel="fused", rho0=(0.0, 0.0),
                  body_force=(0.0, 0.0, 0.0), ckpt_every=0, ckpt_steps_max=0, device=None, stream=None,
-                 model="shan_chen", cg=None, max_particles=0, slab_halo=0):
+                 model="shan_chen", cg=None, max_particles=0, slab_halo=0, workspace=None):
         L = _lib.lib()
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.shape = (self.nz, self.ny, self.nx)
@@ -66,7 +66,12 @@ class Solver:
         if nbytes == 0:
             raise ValueError("invalid grid or options")
         self.device = torch.device(device if device is not None else "cuda")
-        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        if workspace is None:
+            self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        else:   # a caller's uint8 device tensor, 256-byte aligned, at least lb_workspace_bytes long
+            if workspace.dtype != torch.uint8 or not workspace.is_cuda or workspace.numel() < nbytes:
+                raise ValueError("workspace must be a uint8 CUDA tensor of at least %d bytes" % nbytes)
+            self.workspace = workspace
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.mask = None
         mptr = None
