@@ -271,6 +271,14 @@ __device__ __forceinline__ void sums(const float (&d)[2][Q], float& dA, float& d
     momentum<S>(d, j);
 }
 
+// BGK arithmetic of storage type S: 16-bit storage (bound by instruction
+// issue) takes the form with fewer operations (the pair's coefficients
+// precomputed, c.u without an addition to zero: three fewer per pair and component);
+// FP32 (bound by memory bandwidth) keeps the form that schedules faster
+// there. Every kernel of one storage type uses the same form.
+template <typename S>
+constexpr bool kLeanBGK = sizeof(S) == 2;
+
 // BGK collision with the Shan-Chen velocity shift, in deviation form, and
 // store of the post-collision node.
 //   SA, SB: sum_{i>=1} w_i psi^k(x + c_i) c_i for k = A, B.
@@ -306,11 +314,6 @@ __device__ __forceinline__ void collide_store_g(DGet&& dget, const Phys& p, floa
 #pragma unroll
         for (int a = 0; a < 3; ++a) u[a] = up[a] + p.tau * (p.g[a] - p.G * Sk[a]);
         const float uu15 = 1.5f * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-        // omega * f^eq deviation, split for an opposite pair (i, i+1) into a
-        // part even in c (w (drho + rho (4.5 (c.u)^2 - 1.5 u.u))) and a part
-        // odd in c (3 w rho c.u)
-        const float wr1 = p.omega * (1.0f / 18.0f) * rk, wd1 = p.omega * (1.0f / 18.0f) * drk;
-        const float wr2 = p.omega * (1.0f / 36.0f) * rk, wd2 = p.omega * (1.0f / 36.0f) * drk;
         auto put = [&](int i, float v) {
             if (k == 0) {
                 gA[i] = v;
@@ -320,20 +323,53 @@ __device__ __forceinline__ void collide_store_g(DGet&& dget, const Phys& p, floa
                 Store<S>::st2(out + i * (2 * kBlk), a, b);
             }
         };
-        put(0, om1 * dget(k, 0) + p.omega * (1.0f / 3.0f) * (drk - rk * uu15));
-        static_for<0, 9>([&](auto M) {
-            constexpr int i = 2 * decltype(M)::value + 1;   // (i, i + 1) opposite
-            float cu = 0.f;
-            if constexpr (Vel<i>::x != 0) cu += Vel<i>::x * u[0];
-            if constexpr (Vel<i>::y != 0) cu += Vel<i>::y * u[1];
-            if constexpr (Vel<i>::z != 0) cu += Vel<i>::z * u[2];
-            constexpr bool axis = Vel<i>::c2 == 1;
-            const float wr = axis ? wr1 : wr2, wd = axis ? wd1 : wd2;
-            const float even = wr * (4.5f * cu * cu - uu15) + wd;
-            const float odd = 3.0f * wr * cu;
-            put(i, om1 * dget(k, i) + (even + odd));
-            put(i + 1, om1 * dget(k, i + 1) + (even - odd));
-        });
+        if constexpr (kLeanBGK<S>) {
+            // omega * f^eq deviation, split for an opposite pair (i, i+1) of
+            // weight w into a part even in c, w (drho + rho (4.5 (c.u)^2 -
+            // 1.5 u.u)) = a (c.u)^2 + e, and a part odd in c, 3 w rho c.u =
+            // b c.u, with a = 4.5 w rho, b = 3 w rho, e = w (drho - 1.5 rho
+            // u.u) (all times omega). The diagonal weight is half the axis
+            // weight, so its three coefficients are the axis ones halved
+            // (exactly).
+            const float wr1 = p.omega * (1.0f / 18.0f) * rk;
+            const float a1 = 4.5f * wr1, b1 = 3.0f * wr1;
+            const float e1 = fmaf(-wr1, uu15, p.omega * (1.0f / 18.0f) * drk);
+            const float a2 = 0.5f * a1, b2 = 0.5f * b1, e2 = 0.5f * e1;
+            // rest population (weight 1/3 = 6 x 1/18): omega f^eq deviation 6 e
+            put(0, fmaf(om1, dget(k, 0), 6.0f * e1));
+            static_for<0, 9>([&](auto M) {
+                constexpr int i = 2 * decltype(M)::value + 1;   // (i, i + 1) opposite
+                // c.u from the nonzero components only (no addition to 0)
+                constexpr int ax0 = vel_axis0<i>(), ax1 = vel_axis1<i>();
+                float cu = vel_comp<i, ax0>() > 0 ? u[ax0] : -u[ax0];
+                if constexpr (Vel<i>::c2 == 2) cu = vel_comp<i, ax1>() > 0 ? cu + u[ax1] : cu - u[ax1];
+                constexpr bool axis = Vel<i>::c2 == 1;
+                const float ca = axis ? a1 : a2, cb = axis ? b1 : b2, ce = axis ? e1 : e2;
+                const float even = fmaf(ca, cu * cu, ce);
+                put(i, fmaf(cb, cu, fmaf(om1, dget(k, i), even)));
+                put(i + 1, fmaf(-cb, cu, fmaf(om1, dget(k, i + 1), even)));
+            });
+        } else {
+            // omega * f^eq deviation, split for an opposite pair (i, i+1) into
+            // a part even in c (w (drho + rho (4.5 (c.u)^2 - 1.5 u.u))) and a
+            // part odd in c (3 w rho c.u)
+            const float wr1 = p.omega * (1.0f / 18.0f) * rk, wd1 = p.omega * (1.0f / 18.0f) * drk;
+            const float wr2 = p.omega * (1.0f / 36.0f) * rk, wd2 = p.omega * (1.0f / 36.0f) * drk;
+            put(0, om1 * dget(k, 0) + p.omega * (1.0f / 3.0f) * (drk - rk * uu15));
+            static_for<0, 9>([&](auto M) {
+                constexpr int i = 2 * decltype(M)::value + 1;   // (i, i + 1) opposite
+                float cu = 0.f;
+                if constexpr (Vel<i>::x != 0) cu += Vel<i>::x * u[0];
+                if constexpr (Vel<i>::y != 0) cu += Vel<i>::y * u[1];
+                if constexpr (Vel<i>::z != 0) cu += Vel<i>::z * u[2];
+                constexpr bool axis = Vel<i>::c2 == 1;
+                const float wr = axis ? wr1 : wr2, wd = axis ? wd1 : wd2;
+                const float even = wr * (4.5f * cu * cu - uu15) + wd;
+                const float odd = 3.0f * wr * cu;
+                put(i, om1 * dget(k, i) + (even + odd));
+                put(i + 1, om1 * dget(k, i + 1) + (even - odd));
+            });
+        }
     }
 }
 
