@@ -394,14 +394,18 @@ template <typename S, typename DGet>
 __device__ __forceinline__ void cg_collide_store_g(DGet&& dget, const Phys& p, float dA, float dB,
                                                    const float (&j)[3], const float (&gt)[3],
                                                    S* __restrict__ dst, int own) {
+    // Every sum of products is written as explicit fused multiply-adds, so
+    // that no kernel's compilation can contract it differently: the box and
+    // the two-pass kernels give the same bits.
     const float rA = p.rho0[0] + dA, rB = p.rho0[1] + dB;
-    const float inv = __fdividef(1.0f, rA + rB);
+    const float rho = rA + rB, drho = dA + dB;
+    const float inv = __fdividef(1.0f, rho);
     const float u[3] = {j[0] * inv, j[1] * inv, j[2] * inv};
-    const float uu15 = 1.5f * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-    const float inu = (rA * p.cg_inu[0] + rB * p.cg_inu[1]) * inv;   // 1 / nu_bar
-    const float omega = __fdividef(2.0f * inu, 6.0f + inu);           // 2 / (6 nu_bar + 1)
+    const float uu15 = 1.5f * fmaf(u[2], u[2], fmaf(u[1], u[1], u[0] * u[0]));
+    const float inu = fmaf(rA, p.cg_inu[0], rB * p.cg_inu[1]) * inv;   // 1 / nu_bar
+    const float omega = __fdividef(2.0f * inu, 6.0f + inu);             // 2 / (6 nu_bar + 1)
     const float om1 = 1.0f - omega;
-    const float g2 = gt[0] * gt[0] + gt[1] * gt[1] + gt[2] * gt[2];
+    const float g2 = fmaf(gt[2], gt[2], fmaf(gt[1], gt[1], gt[0] * gt[0]));
     // 1 / |grad Theta|; 0 (no perturbation, no recolouring) where |grad Theta|
     // <= 1e-5: the direction of a gradient at the rounding level of the state
     // is undefined, and cos(phi_i) has no limit at grad Theta = 0
@@ -409,37 +413,49 @@ __device__ __forceinline__ void cg_collide_store_g(DGet&& dget, const Phys& p, f
     const float gn = g2 * q;                           // |grad Theta|
     const float hA = 1.125f * omega * p.cg_sigma;     // A / 2
     const float kc = p.cg_beta * rA * rB * inv * q;   // beta rho^A rho^B / (rho |grad Theta|)
-    const float e = (rA * p.rho0[1] - p.rho0[0] * rB) * inv;
+    const float e = fmaf(rA, p.rho0[1], -(p.rho0[0] * rB)) * inv;
     const float fa = rA * inv, fb = rB * inv;
     S* out = dst + blk_base((uint32_t)own);
+    // The two components' BGK terms enter only through their sum D_i, so they
+    // are added first, and each opposite pair's coefficients are formed once
+    // per weight class (the diagonal ones are the axis ones halved, exactly):
+    //   D_i = (1 - omega) (d_i^A + d_i^B) + E + a (c.u)^2 + P (c.gT)^2 + b c.u,
+    // E = omega w (drho - 1.5 rho u.u) - 2 (A/2) B_i |gT|, a = 4.5 omega w rho,
+    // P = 2 (A/2) w / |gT|, b = 3 omega w rho (gT = grad Theta); c.u and c.gT
+    // change sign within a pair, the perturbation does not, and the
+    // recolouring term X = beta rho^A rho^B / (rho |gT|) (w / |c|) c.gT flips.
+    const float base = omega * fmaf(-rho, uu15, drho);   // omega (drho - 1.5 rho u.u)
     {   // rest velocity: c = 0, so no recolouring
         constexpr float w = 1.0f / 3.0f;
-        const float pert = hA * ((2.0f / 9.0f) * gn);
-        const float D = (om1 * dget(0, 0) + omega * w * (dA - rA * uu15) + pert) +
-                        (om1 * dget(1, 0) + omega * w * (dB - rB * uu15) + pert);
-        Store<S>::st2(out, w * e + fa * D, -w * e + fb * D);
+        const float D = fmaf(om1, dget(0, 0) + dget(1, 0), fmaf(w, base, hA * ((4.0f / 9.0f) * gn)));
+        Store<S>::st2(out, fmaf(fa, D, w * e), fmaf(fb, D, -(w * e)));
     }
-    // opposite pairs (i, i + 1): c.u, c.grad Theta change sign, the
-    // perturbation is the same and the recolouring term flips
+    const float orho = omega * rho;
+    const float E1 = fmaf(-2.0f * hA * (1.0f / 54.0f), gn, (1.0f / 18.0f) * base);
+    const float E2 = fmaf(-2.0f * hA * (1.0f / 27.0f), gn, (1.0f / 36.0f) * base);
+    const float a1 = (4.5f / 18.0f) * orho, a2 = 0.5f * a1;
+    const float b1 = (3.0f / 18.0f) * orho, b2 = 0.5f * b1;
+    const float P1 = (2.0f / 18.0f) * hA * q, P2 = 0.5f * P1;
+    const float X1 = kc * (1.0f / 18.0f), X2 = kc * (0.70710678f / 36.0f);   // w / |c|: 1/18, 1/(36 sqrt 2)
+    const float we1 = (1.0f / 18.0f) * e, we2 = 0.5f * we1;
     static_for<0, 9>([&](auto M) {
-        constexpr int i = 2 * decltype(M)::value + 1;
-        float cu = 0.f, cg = 0.f;
-        if constexpr (Vel<i>::x != 0) { cu += Vel<i>::x * u[0]; cg += Vel<i>::x * gt[0]; }
-        if constexpr (Vel<i>::y != 0) { cu += Vel<i>::y * u[1]; cg += Vel<i>::y * gt[1]; }
-        if constexpr (Vel<i>::z != 0) { cu += Vel<i>::z * u[2]; cg += Vel<i>::z * gt[2]; }
-        constexpr float w = wgt<i>();
-        constexpr float Bi = Vel<i>::c2 == 1 ? 1.0f / 54.0f : 1.0f / 27.0f;
-        constexpr float wrc = Vel<i>::c2 == 2 ? w * 0.70710678f : w;   // w_i / |c_i|
-        const float even = 4.5f * cu * cu - uu15, odd = 3.0f * cu;
-        const float pert = hA * (w * cg * cg * q - Bi * gn);
-        const float ow = omega * w;
-        const float bA = ow * (dA + rA * even) + pert, oA = ow * rA * odd;
-        const float bB = ow * (dB + rB * even) + pert, oB = ow * rB * odd;
-        const float Di = (om1 * dget(0, i) + bA + oA) + (om1 * dget(1, i) + bB + oB);
-        const float Dj = (om1 * dget(0, i + 1) + bA - oA) + (om1 * dget(1, i + 1) + bB - oB);
-        const float X = kc * wrc * cg, we = w * e;
-        Store<S>::st2(out + i * (2 * kBlk), we + fa * Di + X, -we + fb * Di - X);
-        Store<S>::st2(out + (i + 1) * (2 * kBlk), we + fa * Dj - X, -we + fb * Dj + X);
+        constexpr int i = 2 * decltype(M)::value + 1;   // (i, i + 1) opposite
+        constexpr int ax0 = vel_axis0<i>(), ax1 = vel_axis1<i>();
+        float cu = vel_comp<i, ax0>() > 0 ? u[ax0] : -u[ax0];
+        float cg = vel_comp<i, ax0>() > 0 ? gt[ax0] : -gt[ax0];
+        if constexpr (Vel<i>::c2 == 2) {
+            cu = vel_comp<i, ax1>() > 0 ? cu + u[ax1] : cu - u[ax1];
+            cg = vel_comp<i, ax1>() > 0 ? cg + gt[ax1] : cg - gt[ax1];
+        }
+        constexpr bool axis = Vel<i>::c2 == 1;
+        const float Ec = axis ? E1 : E2, ac = axis ? a1 : a2, bc = axis ? b1 : b2;
+        const float Pc = axis ? P1 : P2, Xc = axis ? X1 : X2, we = axis ? we1 : we2;
+        const float even = fmaf(ac, cu * cu, fmaf(Pc, cg * cg, Ec));
+        const float Di = fmaf(bc, cu, fmaf(om1, dget(0, i) + dget(1, i), even));
+        const float Dj = fmaf(-bc, cu, fmaf(om1, dget(0, i + 1) + dget(1, i + 1), even));
+        const float X = Xc * cg;
+        Store<S>::st2(out + i * (2 * kBlk), fmaf(fa, Di, we) + X, fmaf(fb, Di, -we) - X);
+        Store<S>::st2(out + (i + 1) * (2 * kBlk), fmaf(fa, Dj, we) - X, fmaf(fb, Dj, -we) + X);
     });
 }
 
