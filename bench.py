@@ -526,11 +526,12 @@ def other_workloads(peak, peak_kind, steps=200, warmup=10):
                                      "launches_per_step": info["launches_per_step"]}
     del Wc
     Wg = workload("cg256")
-    ms, info, _ = time_device(Wg, "fp32", "fused", steps, warmup)
-    step_s = ms / 1e3 / steps
-    out["cg256_fp32"] = {"GLUPS": N / step_s / 1e9, "ms_per_step": step_s * 1e3,
-                         "hbm_frac_of_%s" % peak_kind: 304 * N / step_s / 1e9 / peak,
-                         "paper_V100_GLUPS_context": 0.601}
+    for prec in ("fp32", "fp16", "bf16"):
+        ms, info, _ = time_device(Wg, prec, "fused", steps, warmup)
+        step_s = ms / 1e3 / steps
+        out["cg256_" + prec] = {"GLUPS": N / step_s / 1e9, "ms_per_step": step_s * 1e3,
+                                "hbm_frac_of_%s" % peak_kind: BYTES_PER_SITE[prec] * N / step_s / 1e9 / peak,
+                                "paper_V100_GLUPS_context": 0.601}
     del Wg
     Ws = workload("single256")
     ms, info, _ = time_single(Ws, "fp32", steps, warmup)
