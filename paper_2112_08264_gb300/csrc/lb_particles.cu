@@ -24,11 +24,6 @@ namespace {
 
 constexpr int kPT = 256;   // threads per sphere block
 
-__device__ __forceinline__ int wrapn(int a, int n) {
-    a %= n;
-    return a < 0 ? a + n : a;
-}
-
 // minimum-image displacement along one axis of period n (general form)
 __device__ __forceinline__ double min_image(double d, int n) {
     return __dsub_rn(d, __dmul_rn((double)n, rint(__ddiv_rn(d, (double)n))));
@@ -58,14 +53,15 @@ struct Cube {
             lo[a] = base[a] - half;
         }
     }
-    __device__ int count() const { return side * side * side; }
-    __device__ void at(int b, const Geom& g, int (&u)[3], int (&x)[3]) const {
-        u[0] = lo[0] + b % side;
-        u[1] = lo[1] + (b / side) % side;
-        u[2] = lo[2] + b / (side * side);
-        x[0] = wrapn(u[0], g.nx);
-        x[1] = wrapn(u[1], g.ny);
-        x[2] = wrapn(u[2], g.nz);
+    // site (bx, by, bz) of the cube; u stays within one period of the grid
+    // (0 <= floor(c) < n and half + 1 < n), so one conditional wrap gives x
+    __device__ void site(int bx, int by, int bz, const Geom& g, int (&u)[3], int (&x)[3]) const {
+        u[0] = lo[0] + bx;
+        u[1] = lo[1] + by;
+        u[2] = lo[2] + bz;
+        const int n[3] = {g.nx, g.ny, g.nz};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) x[a] = u[a] < 0 ? u[a] + n[a] : (u[a] >= n[a] ? u[a] - n[a] : u[a]);
     }
     // approximate squared distance from the centre (FP32, for shell tests)
     __device__ float dist2(const int (&u)[3], float (&d)[3]) const {
@@ -74,6 +70,46 @@ struct Cube {
         return d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
     }
 };
+
+// A walk over the cube's sites without a division per site: thread t of a
+// block of nt threads visits the sites b = t, t + nt, t + 2 nt, ... of the
+// side^3 cube (b = bx + side (by + side bz)); stepping adds nt in the same
+// base-side digits.
+struct CubeWalk {
+    int side;
+    int bx, by, bz;      // this thread's current site
+    int dbx, dby, dbz;   // nt in those digits
+    __device__ CubeWalk(const Cube& cube, int t, int nt) : side(cube.side) {
+        split(t, bx, by, bz);
+        split(nt, dbx, dby, dbz);
+    }
+    __device__ void split(int j, int& a, int& b, int& c) const {
+        a = j % side;
+        const int q = j / side;
+        b = q % side;
+        c = q / side;
+    }
+    __device__ bool valid() const { return bz < side; }
+    __device__ void next() {
+        bx += dbx;
+        if (bx >= side) { bx -= side; ++by; }
+        by += dby;
+        if (by >= side) { by -= side; ++bz; }
+        bz += dbz;
+    }
+};
+
+// f(u, x, r2, d) for every site of the cube, over the block's threads
+template <typename F>
+__device__ __forceinline__ void for_cube(const Cube& cube, const Geom& g, F&& f) {
+    for (CubeWalk wk(cube, threadIdx.x, blockDim.x); wk.valid(); wk.next()) {
+        int u[3], x[3];
+        cube.site(wk.bx, wk.by, wk.bz, g, u, x);
+        float d[3];
+        const float r2 = cube.dist2(u, d);
+        f(u, x, r2, d);
+    }
+}
 
 // exact minimum-image displacement of grid coordinate x (unwrapped u) from c
 __device__ __forceinline__ double disp(int x, int u, double c, int n) {
@@ -111,8 +147,9 @@ __device__ __forceinline__ uint32_t site_of(const int (&x)[3], const Geom& g) {
     return (uint32_t)x[0] + (uint32_t)g.nx * ((uint32_t)x[1] + (uint32_t)g.ny * (uint32_t)x[2]);
 }
 
-// This thread's nodes of a sphere's cube (b = threadIdx.x + k kPT), eight at a
-// time: cand(u, x, r2) picks the nodes to visit (it is called for every node),
+// This thread's nodes of a sphere's cube (its sites of the cube walk), eight
+// steps at a time: cand(u, x, r2) picks the nodes to visit (it is called for
+// every node),
 // the owner of every picked node of the batch is loaded first -- independent
 // loads whose DRAM round trips overlap, where one load per node in turn
 // would wait for each -- and then body(u, x, r2, owner) runs for each.
@@ -123,33 +160,38 @@ template <typename Cand, typename Body>
 __device__ __forceinline__ void cube_batches(const Cube& cube, const Geom& g, const int* owner, Cand&& cand,
                                              Body&& body) {
     constexpr int kB = 8;
-    for (int b0 = threadIdx.x; b0 < cube.count(); b0 += kB * kPT) {
+    CubeWalk wk(cube, threadIdx.x, blockDim.x);
+    while (wk.valid()) {
+        const CubeWalk w0 = wk;
         int own[kB];
         bool ok[kB];
 #pragma unroll
         for (int k = 0; k < kB; ++k) {
-            const int b = b0 + k * kPT;
             ok[k] = false;
             own[k] = 0;
-            if (b < cube.count()) {
+            if (wk.valid()) {
                 int u[3], x[3];
-                cube.at(b, g, u, x);
+                cube.site(wk.bx, wk.by, wk.bz, g, u, x);
                 float df[3];
                 const float r2 = cube.dist2(u, df);
                 if (cand(u, x, r2)) {
                     ok[k] = true;
                     own[k] = __ldg(owner + site_of(x, g));
                 }
+                wk.next();
             }
         }
+        CubeWalk w1 = w0;
 #pragma unroll
         for (int k = 0; k < kB; ++k) {
-            if (!ok[k]) continue;
-            int u[3], x[3];
-            cube.at(b0 + k * kPT, g, u, x);
-            float df[3];
-            const float r2 = cube.dist2(u, df);
-            body(u, x, r2, own[k]);
+            if (ok[k]) {
+                int u[3], x[3];
+                cube.site(w1.bx, w1.by, w1.bz, g, u, x);
+                float df[3];
+                const float r2 = cube.dist2(u, df);
+                body(u, x, r2, own[k]);
+            }
+            w1.next();
         }
     }
 }
@@ -209,15 +251,11 @@ __global__ void __launch_bounds__(kPT) sphere_links_kernel(S* __restrict__ st, c
     const float hi2 = (float)((A.radius + 2.0) * (A.radius + 2.0));
     int gF[3] = {0, 0, 0}, gT[3] = {0, 0, 0};   // sum 36 w_i c_i, sum 36 w_i (2 (u - base) + c_i) x c_i
     float dF[3] = {0.f, 0.f, 0.f}, dT[3] = {0.f, 0.f, 0.f};
-    for (int b = threadIdx.x; b < cube.count(); b += kPT) {
-        int u[3], x[3];
-        cube.at(b, g, u, x);
-        float d[3];
-        const float r2 = cube.dist2(u, d);
-        if (r2 <= lo2 || r2 > hi2) continue;
+    for_cube(cube, g, [&](const int (&u)[3], const int (&x)[3], float r2, const float (&d)[3]) {
+        if (r2 <= lo2 || r2 > hi2) return;
         const uint32_t s = site_of(x, g);
         const uint32_t fl = __ldg(flags + s);
-        if ((fl & kSolid) || !(fl & kNbSolidMask)) continue;
+        if ((fl & kSolid) || !(fl & kNbSolidMask)) return;
         const int xm = wrap_dec(x[0], g.nx), xp = wrap_inc(x[0], g.nx);
         const int ym = wrap_dec(x[1], g.ny), yp = wrap_inc(x[1], g.ny);
         const int zm = wrap_dec(x[2], g.nz), zp = wrap_inc(x[2], g.nz);
@@ -277,7 +315,7 @@ __global__ void __launch_bounds__(kPT) sphere_links_kernel(S* __restrict__ st, c
                 dT[a] += Tq[a];
             }
         });
-    }
+    });
     if (!forces) return;
     double acc[12];
 #pragma unroll
@@ -391,13 +429,17 @@ __global__ void __launch_bounds__(kPT) sphere_uncover_kernel(S* __restrict__ st,
     const Cube cube(c, A.half);
     const double R2 = __dmul_rn(A.radius, A.radius);
     const float in2 = (float)((A.radius - 2.0) * (A.radius - 2.0));
+    const float out2 = (float)((A.radius + 2.0) * (A.radius + 2.0));
     const double r0 = (double)p.rho0[0] + (double)p.rho0[1];
     if (threadIdx.x == 0) A.moved[q] = 0;
     if (within_margin(A, q, g)) return;   // the whole block: no node changed
     __syncthreads();
     double acc[6] = {0, 0, 0, 0, 0, 0};
-    // deep inside (beyond R - 2): still covered
-    auto cand = [&](const int (&)[3], const int (&)[3], float r2) { return !(A.radius > 2.0 && r2 < in2); };
+    // deep inside (beyond R - 2): still covered; beyond R + 2: never covered
+    // (a node the sphere covered lies within R + 1 of the new centre)
+    auto cand = [&](const int (&)[3], const int (&)[3], float r2) {
+        return !(A.radius > 2.0 && r2 < in2) && r2 <= out2;
+    };
     cube_batches(cube, g, A.owner, cand, [&](const int (&u)[3], const int (&x)[3], float r2, int own) {
         if (own != q + 1) return;
         if (covered(u, x, r2, c, R2, g)) return;
@@ -544,14 +586,10 @@ __global__ void sphere_flags_kernel(uint32_t* __restrict__ flags, const uint8_t*
     const Cube cube(c, A.half + 1);
     const float in2 = A.radius > 3.5 ? (float)((A.radius - 3.5) * (A.radius - 3.5)) : -1.f;
     const float out2 = (float)((A.radius + 3.5) * (A.radius + 3.5));
-    for (int b = threadIdx.x; b < cube.count(); b += kPT) {
-        int u[3], x[3];
-        cube.at(b, g, u, x);
-        float df[3];
-        const float r2 = cube.dist2(u, df);
-        if (r2 < in2 || r2 > out2) continue;
+    for_cube(cube, g, [&](const int (&)[3], const int (&x)[3], float r2, const float (&)[3]) {
+        if (r2 < in2 || r2 > out2) return;
         one(x[0], x[1], x[2]);
-    }
+    });
 }
 
 template <typename F32, typename F16, typename BF16>
