@@ -119,9 +119,10 @@ __device__ __forceinline__ double disp(int x, int u, double c, int n) {
 
 // Is the site within radius of the centre? Far from the sphere's surface the
 // FP32 distance decides; near it, the exact FP64 test (the oracle's rule).
+// R2f = (float)R2, formed once by the caller (a conversion from FP64 per site
+// would run on the FP64 pipe).
 __device__ __forceinline__ bool covered(const int (&u)[3], const int (&x)[3], float r2f, const double* c, double R2,
-                                        const Geom& g) {
-    const float R2f = (float)R2;
+                                        float R2f, const Geom& g) {
     if (r2f < 0.99f * R2f) return true;
     if (r2f > 1.01f * R2f) return false;
     return norm2(disp(x[0], u[0], c[0], g.nx), disp(x[1], u[1], c[1], g.ny), disp(x[2], u[2], c[2], g.nz)) <= R2;
@@ -428,21 +429,20 @@ __global__ void __launch_bounds__(kPT) sphere_uncover_kernel(S* __restrict__ st,
     load3(A.w, q, w);
     const Cube cube(c, A.half);
     const double R2 = __dmul_rn(A.radius, A.radius);
-    const float in2 = (float)((A.radius - 2.0) * (A.radius - 2.0));
+    const float R2f = (float)R2;
+    // deep inside (beyond R - 2): still covered; beyond R + 2: never covered
+    // (a node the sphere covered lies within R + 1 of the new centre)
+    const float in2 = A.radius > 2.0 ? (float)((A.radius - 2.0) * (A.radius - 2.0)) : -1.f;
     const float out2 = (float)((A.radius + 2.0) * (A.radius + 2.0));
     const double r0 = (double)p.rho0[0] + (double)p.rho0[1];
     if (threadIdx.x == 0) A.moved[q] = 0;
     if (within_margin(A, q, g)) return;   // the whole block: no node changed
     __syncthreads();
     double acc[6] = {0, 0, 0, 0, 0, 0};
-    // deep inside (beyond R - 2): still covered; beyond R + 2: never covered
-    // (a node the sphere covered lies within R + 1 of the new centre)
-    auto cand = [&](const int (&)[3], const int (&)[3], float r2) {
-        return !(A.radius > 2.0 && r2 < in2) && r2 <= out2;
-    };
+    auto cand = [&](const int (&)[3], const int (&)[3], float r2) { return !(r2 < in2) && r2 <= out2; };
     cube_batches(cube, g, A.owner, cand, [&](const int (&u)[3], const int (&x)[3], float r2, int own) {
         if (own != q + 1) return;
-        if (covered(u, x, r2, c, R2, g)) return;
+        if (covered(u, x, r2, c, R2, R2f, g)) return;
         const uint32_t s = site_of(x, g);
         A.owner[s] = 0;
         A.moved[q] = 1;
@@ -490,6 +490,7 @@ __global__ void __launch_bounds__(kPT) sphere_cover_kernel(S* __restrict__ st, c
     const Cube cube(c, A.half);
     if (absorb && within_margin(A, q, g)) return;
     const double R2 = __dmul_rn(A.radius, A.radius);
+    const float R2f = (float)R2;
     const float in2 = absorb && A.radius > 2.0 ? (float)((A.radius - 2.0) * (A.radius - 2.0)) : -1.f;
     const float Rf = (float)A.radius;
     float margin = 1e30f;   // distance from the surface of the nearest node
@@ -497,7 +498,7 @@ __global__ void __launch_bounds__(kPT) sphere_cover_kernel(S* __restrict__ st, c
     auto cand = [&](const int (&u)[3], const int (&x)[3], float r2) {
         margin = fminf(margin, fabsf(sqrtf(r2) - Rf));
         // covered now, and not already deep inside before the move
-        return !(r2 < in2) && covered(u, x, r2, c, R2, g);
+        return !(r2 < in2) && covered(u, x, r2, c, R2, R2f, g);
     };
     cube_batches(cube, g, A.owner, cand, [&](const int (&u)[3], const int (&x)[3], float, int own) {
         if (own == q + 1) return;   // covered before
