@@ -118,6 +118,10 @@ struct Spheres {
     // has moved less than that changes no node
     double* ref = nullptr;
     float* margin = nullptr;
+    // per sphere: how far the last leap-frog update moved its centre (|v|,
+    // rounded up); the re-meshing's owners are the coverage at the centre
+    // before that move
+    float* step = nullptr;
     int n = 0;
     double radius = 0.0, mass = 0.0, inertia = 0.0;
     double contact_k = 0.0, contact_range = 0.0;   // k (2R + range - d)^(3/2) for d < 2R + range

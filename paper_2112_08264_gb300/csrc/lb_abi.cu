@@ -101,8 +101,8 @@ Layout make_layout(int nx, int ny, int nz, const lb_options& o) {
     if (o.max_particles > 0) {
         L.owner = off; off += align256(N * 4);   // sphere covering each site
         // r, v, w, F, T, F_c, ref (3 doubles each per sphere), the error word, and per sphere a moved
-        // flag and a margin
-        L.spheres = off; off += align256((size_t)o.max_particles * 21 * 8 + 8 + (size_t)o.max_particles * 8);
+        // flag, a margin and the last step's displacement
+        L.spheres = off; off += align256((size_t)o.max_particles * 21 * 8 + 8 + (size_t)o.max_particles * 12);
     }
     if (o.ckpt_every > 0) {
         L.ckpt_slots = (size_t)(o.ckpt_steps_max / o.ckpt_every) + 1;
@@ -312,6 +312,7 @@ lb_status lb_create(int nx, int ny, int nz, float tau, float G, const uint8_t* m
         S.err = reinterpret_cast<int*>(a + 7 * P3);
         S.moved = S.err + 2;   // 8-byte error slot, then the flags
         S.margin = reinterpret_cast<float*>(S.moved + o.max_particles);
+        S.step = S.margin + o.max_particles;
         S.owner = reinterpret_cast<int*>(c->ws + L.owner);
         S.n = 0;
         if (!mask) c->links.sites = reinterpret_cast<const uint32_t*>(c->ws + L.links);   // no static links
@@ -650,6 +651,7 @@ lb_status lb_particles_set(lb_ctx* c, int n, const double* r, const double* v, c
     S.half = half;
     int err = 0;
     if (e == cudaSuccess) e = cudaMemsetAsync(S.err, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess && n > 0) e = cudaMemsetAsync(S.step, 0, (size_t)n * sizeof(float), c->stream);
     if (e == cudaSuccess) e = launch_sphere_place(c->flags, c->has_mask ? c->mask_dev : nullptr, S, c->g, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&err, S.err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);

@@ -400,6 +400,7 @@ __global__ void sphere_update_kernel(Spheres A, Geom g) {
     if (q >= A.n || !(A.mass > 0.0)) return;
     const int n[3] = {g.nx, g.ny, g.nz};
     bool fast = false;
+    double v2 = 0.0;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const double v = __dadd_rn(A.v[3 * q + a],
@@ -412,14 +413,15 @@ __global__ void sphere_update_kernel(Spheres A, Geom g) {
         A.r[3 * q + a] = r;
         A.w[3 * q + a] = __dadd_rn(A.w[3 * q + a], __ddiv_rn(A.T[3 * q + a], A.inertia));
         fast = fast || fabs(v) > 1.0;
+        v2 += v * v;
     }
+    A.step[q] = __double2float_ru(sqrt(v2));
     if (fast) atomicOr(A.err, 2);
 }
 
 // Re-meshing, first pass: nodes sphere q covered and no longer covers become
 // fluid with f^eq(rho0^k, u_b) at the wall velocity there; the sphere loses
-// that momentum (and its moment). A sphere moves at most one node per step,
-// so such nodes lie within R + 2 of the new centre.
+// that momentum (and its moment).
 template <typename S>
 __global__ void __launch_bounds__(kPT) sphere_uncover_kernel(S* __restrict__ st, Spheres A, Geom g, Phys p) {
     const int q = blockIdx.x;
@@ -430,10 +432,14 @@ __global__ void __launch_bounds__(kPT) sphere_uncover_kernel(S* __restrict__ st,
     const Cube cube(c, A.half);
     const double R2 = __dmul_rn(A.radius, A.radius);
     const float R2f = (float)R2;
-    // deep inside (beyond R - 2): still covered; beyond R + 2: never covered
-    // (a node the sphere covered lies within R + 1 of the new centre)
-    const float in2 = A.radius > 2.0 ? (float)((A.radius - 2.0) * (A.radius - 2.0)) : -1.f;
-    const float out2 = (float)((A.radius + 2.0) * (A.radius + 2.0));
+    // The owners are the coverage at the centre before the last move (the
+    // re-meshing of the previous step, or an earlier one within the margin),
+    // which was the step's displacement away: only a node whose distance from
+    // the surface now is at most that (plus slack for the FP32 distances) can
+    // have changed.
+    const float sd = A.step[q] + 1e-3f, Rf = (float)A.radius;
+    const float in2 = Rf > sd ? (Rf - sd) * (Rf - sd) : -1.f;
+    const float out2 = (Rf + sd) * (Rf + sd);
     const double r0 = (double)p.rho0[0] + (double)p.rho0[1];
     if (threadIdx.x == 0) A.moved[q] = 0;
     if (within_margin(A, q, g)) return;   // the whole block: no node changed
@@ -480,7 +486,7 @@ __global__ void __launch_bounds__(kPT) sphere_uncover_kernel(S* __restrict__ st,
 // Re-meshing, second pass (and placement when !absorb): nodes sphere q now
 // covers and did not take its fluid's momentum (and moment); their
 // populations are cleared. A node held by another sphere or by the mask is
-// an error. After a move such nodes lie beyond R - 2 from the centre.
+// an error.
 template <typename S>
 __global__ void __launch_bounds__(kPT) sphere_cover_kernel(S* __restrict__ st, const uint8_t* __restrict__ mask,
                                                           Spheres A, int absorb, Geom g) {
@@ -491,13 +497,17 @@ __global__ void __launch_bounds__(kPT) sphere_cover_kernel(S* __restrict__ st, c
     if (absorb && within_margin(A, q, g)) return;
     const double R2 = __dmul_rn(A.radius, A.radius);
     const float R2f = (float)R2;
-    const float in2 = absorb && A.radius > 2.0 ? (float)((A.radius - 2.0) * (A.radius - 2.0)) : -1.f;
     const float Rf = (float)A.radius;
+    // after a move only nodes within the step's displacement (plus slack) of
+    // the surface can have become covered (the owners are the coverage before
+    // it); a placement takes every node
+    const float sd = A.step[q] + 1e-3f;
+    const float in2 = absorb && Rf > sd ? (Rf - sd) * (Rf - sd) : -1.f;
     float margin = 1e30f;   // distance from the surface of the nearest node
     double acc[6] = {0, 0, 0, 0, 0, 0};
     auto cand = [&](const int (&u)[3], const int (&x)[3], float r2) {
         margin = fminf(margin, fabsf(sqrtf(r2) - Rf));
-        // covered now, and not already deep inside before the move
+        // covered now, and not already inside before the move
         return !(r2 < in2) && covered(u, x, r2, c, R2, R2f, g);
     };
     cube_batches(cube, g, A.owner, cand, [&](const int (&u)[3], const int (&x)[3], float, int own) {
