@@ -568,9 +568,9 @@ __global__ void __launch_bounds__(kPT) sphere_cover_kernel(S* __restrict__ st, c
 }
 
 // Solid flags (bit 0 solid, bit i: x - c_i solid) from the mask and the
-// coverage: over the shell of every sphere's widened cube where a re-meshing
-// can change a flag (within R -/+ 3.5 of the centre), or over the whole
-// grid when whole != 0.
+// coverage: over the shell of every moved sphere's widened cube where its
+// re-meshing can have changed a flag, or over the whole grid when
+// whole != 0.
 __global__ void sphere_flags_kernel(uint32_t* __restrict__ flags, const uint8_t* __restrict__ mask, Spheres A,
                                     int whole, Geom g) {
     auto solid = [&](uint32_t s) { return (mask && mask[s]) || A.owner[s] != 0; };
@@ -595,8 +595,12 @@ __global__ void sphere_flags_kernel(uint32_t* __restrict__ flags, const uint8_t*
     double c[3];
     load3(A.r, q, c);
     const Cube cube(c, A.half + 1);
-    const float in2 = A.radius > 3.5 ? (float)((A.radius - 3.5) * (A.radius - 3.5)) : -1.f;
-    const float out2 = (float)((A.radius + 3.5) * (A.radius + 3.5));
+    // the changed nodes lie within the step's displacement of the surface
+    // (see the re-meshing), and a flag depends on its node and the 18
+    // neighbours within sqrt 2: the shell within that plus 1.5 of the surface
+    const float Rf = (float)A.radius, sd = A.step[q] + 1e-3f + 1.5f;
+    const float in2 = Rf > sd ? (Rf - sd) * (Rf - sd) : -1.f;
+    const float out2 = (Rf + sd) * (Rf + sd);
     for_cube(cube, g, [&](const int (&)[3], const int (&x)[3], float r2, const float (&)[3]) {
         if (r2 < in2 || r2 > out2) return;
         one(x[0], x[1], x[2]);
