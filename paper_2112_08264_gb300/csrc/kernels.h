@@ -122,6 +122,9 @@ struct Spheres {
     // rounded up); the re-meshing's owners are the coverage at the centre
     // before that move
     float* step = nullptr;
+    // per sphere: the centre in FP32 (x, y, z, 0), for the pair distance
+    // screen of the contact forces (written where the centre changes)
+    float4* rf = nullptr;
     int n = 0;
     double radius = 0.0, mass = 0.0, inertia = 0.0;
     double contact_k = 0.0, contact_range = 0.0;   // k (2R + range - d)^(3/2) for d < 2R + range

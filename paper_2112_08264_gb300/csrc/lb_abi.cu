@@ -41,7 +41,7 @@ namespace {
 size_t store_bytes(int prec) { return prec == LB_FP32 ? 4 : 2; }
 
 struct Layout {
-    size_t pop[2], mask, flags, links, tent, tstart, cursor, rho, red_part, red_out, owner, spheres;
+    size_t pop[2], mask, flags, links, tent, tstart, cursor, rho, red_part, red_out, owner, spheres, rf;
     size_t ckpt, ckpt_slots, seg, adj;
     size_t state_bytes;
     size_t total;
@@ -101,8 +101,9 @@ Layout make_layout(int nx, int ny, int nz, const lb_options& o) {
     if (o.max_particles > 0) {
         L.owner = off; off += align256(N * 4);   // sphere covering each site
         // r, v, w, F, T, F_c, ref (3 doubles each per sphere), the error word, and per sphere a moved
-        // flag, a margin and the last step's displacement
+        // flag, a margin and the last step's displacement; then the FP32 centres
         L.spheres = off; off += align256((size_t)o.max_particles * 21 * 8 + 8 + (size_t)o.max_particles * 12);
+        L.rf = off; off += align256((size_t)o.max_particles * 16);
     }
     if (o.ckpt_every > 0) {
         L.ckpt_slots = (size_t)(o.ckpt_steps_max / o.ckpt_every) + 1;
@@ -313,6 +314,7 @@ lb_status lb_create(int nx, int ny, int nz, float tau, float G, const uint8_t* m
         S.moved = S.err + 2;   // 8-byte error slot, then the flags
         S.margin = reinterpret_cast<float*>(S.moved + o.max_particles);
         S.step = S.margin + o.max_particles;
+        S.rf = reinterpret_cast<float4*>(c->ws + L.rf);
         S.owner = reinterpret_cast<int*>(c->ws + L.owner);
         S.n = 0;
         if (!mask) c->links.sites = reinterpret_cast<const uint32_t*>(c->ws + L.links);   // no static links

@@ -357,17 +357,22 @@ __global__ void __launch_bounds__(kCT) sphere_contact_kernel(Spheres A, Geom g) 
     const float near2 = (float)((far + 0.5) * (far + 0.5));
     const double lub = 1.5 * 3.14159265358979323846 * A.mu * A.radius * A.radius;
     double c[3];
-    float cf[3];
     load3(A.r, q, c);
-    load3(A.r, q, cf);
+    const float4 cq = A.rf[q];
+    const float cf[3] = {cq.x, cq.y, cq.z};
     double F[3] = {0, 0, 0};
     for (int j = threadIdx.x; j < A.n; j += kCT) {
         if (j == q) continue;
+        // FP32 screen on the FP32 centres (0 <= r < n, so one conditional
+        // wrap gives the minimum image)
+        const float4 cj = A.rf[j];
+        const float cjf[3] = {cj.x, cj.y, cj.z};
         float e2 = 0.f;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            float d = cf[a] - (float)A.r[3 * j + a];
-            d -= (float)n[a] * rintf(d / (float)n[a]);
+            float d = cf[a] - cjf[a];
+            const float h = 0.5f * (float)n[a];
+            d = d > h ? d - (float)n[a] : (d < -h ? d + (float)n[a] : d);
             e2 += d * d;
         }
         if (e2 >= near2) continue;
@@ -416,6 +421,7 @@ __global__ void sphere_update_kernel(Spheres A, Geom g) {
         v2 += v * v;
     }
     A.step[q] = __double2float_ru(sqrt(v2));
+    A.rf[q] = make_float4((float)A.r[3 * q], (float)A.r[3 * q + 1], (float)A.r[3 * q + 2], 0.f);
     if (fast) atomicOr(A.err, 2);
 }
 
@@ -556,6 +562,7 @@ __global__ void __launch_bounds__(kPT) sphere_cover_kernel(S* __restrict__ st, c
         A.margin[q] = fminf(mred[0], 1.0f);
 #pragma unroll
         for (int a = 0; a < 3; ++a) A.ref[3 * q + a] = c[a];
+        A.rf[q] = make_float4((float)c[0], (float)c[1], (float)c[2], 0.f);   // a placement sets it here
     }
     if (!absorb) return;
     block_sum(acc);
