@@ -236,8 +236,9 @@ __device__ __forceinline__ void load3(const double* a, int q, T (&o)[3]) {
 // midpoint r_b = x + c_i / 2, the rest part's force and torque are exact
 // integer sums of the link geometry, scaled once per sphere in FP64; the
 // deviation part and the wall velocity are FP32 per link (as the state is),
-// summed in FP64 across the block. Only the shell of sites between R - 1/2
-// and R + 2 from the centre can be linked to the sphere.
+// summed in FP64 across the block. A linked node is fluid (beyond R) with a
+// neighbour inside (within R + sqrt 2): only that shell is visited (with a
+// margin of 0.01 for the FP32 distances).
 template <typename S>
 __global__ void __launch_bounds__(kPT) sphere_links_kernel(S* __restrict__ st, const uint32_t* __restrict__ flags,
                                                           Spheres A, int forces, Geom g, Phys p) {
@@ -248,8 +249,8 @@ __global__ void __launch_bounds__(kPT) sphere_links_kernel(S* __restrict__ st, c
     load3(A.v, q, v);
     load3(A.w, q, w);
     const Cube cube(c, A.half);
-    const float lo2 = (float)((A.radius - 0.5) * (A.radius - 0.5));
-    const float hi2 = (float)((A.radius + 2.0) * (A.radius + 2.0));
+    const float lo2 = (float)((A.radius - 0.01) * (A.radius - 0.01));
+    const float hi2 = (float)((A.radius + 1.4243) * (A.radius + 1.4243));
     int gF[3] = {0, 0, 0}, gT[3] = {0, 0, 0};   // sum 36 w_i c_i, sum 36 w_i (2 (u - base) + c_i) x c_i
     float dF[3] = {0.f, 0.f, 0.f}, dT[3] = {0.f, 0.f, 0.f};
     for_cube(cube, g, [&](const int (&u)[3], const int (&x)[3], float r2, const float (&d)[3]) {
