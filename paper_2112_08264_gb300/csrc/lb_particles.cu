@@ -253,11 +253,8 @@ __global__ void __launch_bounds__(kPT) sphere_links_kernel(S* __restrict__ st, c
     const float hi2 = (float)((A.radius + 1.4243) * (A.radius + 1.4243));
     int gF[3] = {0, 0, 0}, gT[3] = {0, 0, 0};   // sum 36 w_i c_i, sum 36 w_i (2 (u - base) + c_i) x c_i
     float dF[3] = {0.f, 0.f, 0.f}, dT[3] = {0.f, 0.f, 0.f};
-    for_cube(cube, g, [&](const int (&u)[3], const int (&x)[3], float r2, const float (&d)[3]) {
-        if (r2 <= lo2 || r2 > hi2) return;
-        const uint32_t s = site_of(x, g);
-        const uint32_t fl = __ldg(flags + s);
-        if ((fl & kSolid) || !(fl & kNbSolidMask)) return;
+    // the links of one fluid node (site s at x, unwrapped u, offset d from the centre)
+    auto node = [&](const int (&u)[3], const int (&x)[3], const float (&d)[3], uint32_t s, uint32_t fl) {
         const int xm = wrap_dec(x[0], g.nx), xp = wrap_inc(x[0], g.nx);
         const int ym = wrap_dec(x[1], g.ny), yp = wrap_inc(x[1], g.ny);
         const int zm = wrap_dec(x[2], g.nz), zp = wrap_inc(x[2], g.nz);
@@ -317,7 +314,63 @@ __global__ void __launch_bounds__(kPT) sphere_links_kernel(S* __restrict__ st, c
                 dT[a] += Tq[a];
             }
         });
-    });
+    };
+    // In rounds: every thread screens kRound sites of its cube walk (in the
+    // shell, fluid, with a solid neighbour; the flag loads as one batch) and
+    // appends the nodes that pass to a shared list; then the block works the
+    // list one node per thread, so that the link work (a few percent of the
+    // cube's sites) runs on full warps.
+    constexpr int kRound = 8;
+    __shared__ uint32_t lsite[kRound * kPT];   // walk index of each listed node
+    __shared__ uint32_t lflag[kRound * kPT];
+    __shared__ int nlist;
+    const int per_thread = (cube.side * cube.side * cube.side + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int rounds = (per_thread + kRound - 1) / kRound;
+    CubeWalk wk(cube, threadIdx.x, blockDim.x);
+    for (int round = 0; round < rounds; ++round) {
+        if (threadIdx.x == 0) nlist = 0;
+        __syncthreads();
+        uint32_t fl[kRound], idx[kRound];
+        bool in[kRound];
+#pragma unroll
+        for (int k = 0; k < kRound; ++k) {
+            in[k] = false;
+            fl[k] = 0u;
+            idx[k] = 0u;
+            if (wk.valid()) {
+                int u[3], x[3];
+                cube.site(wk.bx, wk.by, wk.bz, g, u, x);
+                float d[3];
+                const float r2 = cube.dist2(u, d);
+                if (r2 > lo2 && r2 <= hi2) {
+                    in[k] = true;
+                    idx[k] = (uint32_t)(wk.bx + cube.side * (wk.by + cube.side * wk.bz));
+                    fl[k] = __ldg(flags + site_of(x, g));
+                }
+                wk.next();
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kRound; ++k) {
+            if (in[k] && !(fl[k] & kSolid) && (fl[k] & kNbSolidMask)) {
+                const int j = atomicAdd(&nlist, 1);
+                lsite[j] = idx[k];
+                lflag[j] = fl[k];
+            }
+        }
+        __syncthreads();
+        const int n = nlist;
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            const int b = (int)lsite[j];
+            const int bx = b % cube.side, byz = b / cube.side;
+            int u[3], x[3];
+            cube.site(bx, byz % cube.side, byz / cube.side, g, u, x);
+            float d[3];
+            cube.dist2(u, d);
+            node(u, x, d, site_of(x, g), lflag[j]);
+        }
+        __syncthreads();   // the list is read before the next round resets it
+    }
     if (!forces) return;
     double acc[12];
 #pragma unroll
