@@ -221,6 +221,33 @@ __device__ void block_sum(double (&v)[NV]) {
     for (int k = 0; k < NV; ++k) v[k] = red[k][0];
 }
 
+// Exclusive prefix sum of v over the block's threads in thread order (block
+// size a multiple of 32, at most 32 warps); *total gets the block's sum.
+// wsum: one int per warp of shared memory. Ends with a barrier.
+__device__ __forceinline__ int block_exclusive_scan(int v, int* wsum, int* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int t = lane < nw ? wsum[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < nw) wsum[lane] = t;   // inclusive warp totals
+        if (lane == nw - 1) *total = t;
+    }
+    __syncthreads();
+    return x - v + (warp > 0 ? wsum[warp - 1] : 0);
+}
+
 template <typename T>
 __device__ __forceinline__ void load3(const double* a, int q, T (&o)[3]) {
 #pragma unroll
@@ -320,16 +347,15 @@ __global__ void __launch_bounds__(kPT) sphere_links_kernel(S* __restrict__ st, c
     // appends the nodes that pass to a shared list; then the block works the
     // list one node per thread, so that the link work (a few percent of the
     // cube's sites) runs on full warps.
-    constexpr int kRound = 8;
+    constexpr int kRound = 10;   // R = 5.5: 4913 sites, 20 a thread, two rounds
     __shared__ uint32_t lsite[kRound * kPT];   // walk index of each listed node
     __shared__ uint32_t lflag[kRound * kPT];
     __shared__ int nlist;
+    __shared__ int wsum[kPT / 32];
     const int per_thread = (cube.side * cube.side * cube.side + (int)blockDim.x - 1) / (int)blockDim.x;
     const int rounds = (per_thread + kRound - 1) / kRound;
     CubeWalk wk(cube, threadIdx.x, blockDim.x);
     for (int round = 0; round < rounds; ++round) {
-        if (threadIdx.x == 0) nlist = 0;
-        __syncthreads();
         uint32_t fl[kRound], idx[kRound];
         bool in[kRound];
 #pragma unroll
@@ -350,12 +376,22 @@ __global__ void __launch_bounds__(kPT) sphere_links_kernel(S* __restrict__ st, c
                 wk.next();
             }
         }
+        // each thread's passing sites go to the list in thread order (a block
+        // scan of the counts), so that the work, and the force sums, are the
+        // same from run to run
+        int cnt = 0;
 #pragma unroll
         for (int k = 0; k < kRound; ++k) {
-            if (in[k] && !(fl[k] & kSolid) && (fl[k] & kNbSolidMask)) {
-                const int j = atomicAdd(&nlist, 1);
+            in[k] = in[k] && !(fl[k] & kSolid) && (fl[k] & kNbSolidMask);
+            cnt += in[k] ? 1 : 0;
+        }
+        int j = block_exclusive_scan(cnt, wsum, &nlist);
+#pragma unroll
+        for (int k = 0; k < kRound; ++k) {
+            if (in[k]) {
                 lsite[j] = idx[k];
                 lflag[j] = fl[k];
+                ++j;
             }
         }
         __syncthreads();
