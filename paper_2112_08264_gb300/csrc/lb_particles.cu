@@ -541,6 +541,7 @@ __global__ void __launch_bounds__(kPT) sphere_uncover_kernel(S* __restrict__ st,
     if (within_margin(A, q, g)) return;   // the whole block: no node changed
     __syncthreads();
     double acc[6] = {0, 0, 0, 0, 0, 0};
+    bool changed = false;
     auto cand = [&](const int (&)[3], const int (&)[3], float r2) { return !(r2 < in2) && r2 <= out2; };
     cube_batches(cube, g, A.owner, cand, [&](const int (&u)[3], const int (&x)[3], float r2, int own) {
         if (own != q + 1) return;
@@ -548,6 +549,7 @@ __global__ void __launch_bounds__(kPT) sphere_uncover_kernel(S* __restrict__ st,
         const uint32_t s = site_of(x, g);
         A.owner[s] = 0;
         A.moved[q] = 1;
+        changed = true;
         const double arm[3] = {disp(x[0], u[0], c[0], g.nx), disp(x[1], u[1], c[1], g.ny),
                                disp(x[2], u[2], c[2], g.nz)};
         double ub[3];
@@ -570,6 +572,7 @@ __global__ void __launch_bounds__(kPT) sphere_uncover_kernel(S* __restrict__ st,
             acc[3 + a] -= r0 * L[a];
         }
     });
+    if (!__syncthreads_or(changed)) return;   // no node changed: nothing to exchange
     block_sum(acc);
     if (threadIdx.x == 0 && A.mass > 0.0)
 #pragma unroll
@@ -601,6 +604,7 @@ __global__ void __launch_bounds__(kPT) sphere_cover_kernel(S* __restrict__ st, c
     const float in2 = absorb && Rf > sd ? (Rf - sd) * (Rf - sd) : -1.f;
     float margin = 1e30f;   // distance from the surface of the nearest node
     double acc[6] = {0, 0, 0, 0, 0, 0};
+    bool changed = false;
     auto cand = [&](const int (&u)[3], const int (&x)[3], float r2) {
         margin = fminf(margin, fabsf(sqrtf(r2) - Rf));
         // covered now, and not already inside before the move
@@ -615,6 +619,7 @@ __global__ void __launch_bounds__(kPT) sphere_cover_kernel(S* __restrict__ st, c
         }
         if (!absorb) return;
         A.moved[q] = 1;
+        changed = true;
         double m[3] = {0, 0, 0};
         static_for<1, Q>([&](auto I) {
             constexpr int i = decltype(I)::value;
@@ -641,20 +646,20 @@ __global__ void __launch_bounds__(kPT) sphere_cover_kernel(S* __restrict__ st, c
     });
     // the margin of this centre (nodes beyond the cube are farther than its
     // half-width, which exceeds R + 1)
-    __shared__ float mred[kPT];
-    mred[threadIdx.x] = margin;
-    __syncthreads();
-    for (int h = kPT / 2; h > 0; h >>= 1) {
-        if ((int)threadIdx.x < h) mred[threadIdx.x] = fminf(mred[threadIdx.x], mred[threadIdx.x + h]);
-        __syncthreads();
-    }
+    __shared__ float mred[kPT / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) margin = fminf(margin, __shfl_xor_sync(0xffffffffu, margin, o));
+    if ((threadIdx.x & 31) == 0) mred[threadIdx.x >> 5] = margin;
+    const bool any = __syncthreads_or(changed);   // also publishes mred
     if (threadIdx.x == 0) {
-        A.margin[q] = fminf(mred[0], 1.0f);
+        float m = mred[0];
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) m = fminf(m, mred[k]);
+        A.margin[q] = fminf(m, 1.0f);
 #pragma unroll
         for (int a = 0; a < 3; ++a) A.ref[3 * q + a] = c[a];
         A.rf[q] = make_float4((float)c[0], (float)c[1], (float)c[2], 0.f);   // a placement sets it here
     }
-    if (!absorb) return;
+    if (!absorb || !any) return;   // a placement, or no node changed: nothing to exchange
     block_sum(acc);
     if (threadIdx.x == 0 && A.mass > 0.0)
 #pragma unroll
