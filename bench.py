@@ -407,7 +407,7 @@ def main_particles(args, W, world, rank, local):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": peak_kind, "algorithmic_bytes_per_site": alg_bytes,
                      "timed": "the whole step (%d launches: sphere links, step kernel, contact, leap-frog, two "
-                              "re-meshing passes, flags)" % info["launches_per_step"],
+                              "re-meshing passes that also update the flags)" % info["launches_per_step"],
                      "traffic": (lambda t: t * N if t is not None and (nx, ny, nz) == (256, 256, 256) else None)(
                          traffic_per_site("particles_" + args.prec))},
         "gpu_launches": args.steps * info["launches_per_step"],

@@ -112,7 +112,6 @@ struct Spheres {
     double* Fc = nullptr;   // contact forces
     int* owner = nullptr;
     int* err = nullptr;
-    int* moved = nullptr;   // per sphere: 1 when the last re-meshing changed a node
     // per sphere: centre at the last full re-meshing pass (3 doubles) and the
     // distance from there of the node nearest to its surface; a sphere that
     // has moved less than that changes no node

@@ -100,9 +100,9 @@ Layout make_layout(int nx, int ny, int nz, const lb_options& o) {
     L.red_out = off; off += align256(kRedVals * 8);
     if (o.max_particles > 0) {
         L.owner = off; off += align256(N * 4);   // sphere covering each site
-        // r, v, w, F, T, F_c, ref (3 doubles each per sphere), the error word, and per sphere a moved
-        // flag, a margin and the last step's displacement; then the FP32 centres
-        L.spheres = off; off += align256((size_t)o.max_particles * 21 * 8 + 8 + (size_t)o.max_particles * 12);
+        // r, v, w, F, T, F_c, ref (3 doubles each per sphere), the error word, and per sphere a
+        // margin and the last step's displacement; then the FP32 centres
+        L.spheres = off; off += align256((size_t)o.max_particles * 21 * 8 + 8 + (size_t)o.max_particles * 8);
         L.rf = off; off += align256((size_t)o.max_particles * 16);
     }
     if (o.ckpt_every > 0) {
@@ -311,8 +311,7 @@ lb_status lb_create(int nx, int ny, int nz, float tau, float G, const uint8_t* m
         S.Fc = a + 5 * P3;
         S.ref = a + 6 * P3;
         S.err = reinterpret_cast<int*>(a + 7 * P3);
-        S.moved = S.err + 2;   // 8-byte error slot, then the flags
-        S.margin = reinterpret_cast<float*>(S.moved + o.max_particles);
+        S.margin = reinterpret_cast<float*>(S.err + 2);   // after the 8-byte error slot
         S.step = S.margin + o.max_particles;
         S.rf = reinterpret_cast<float4*>(c->ws + L.rf);
         S.owner = reinterpret_cast<int*>(c->ws + L.owner);
@@ -551,7 +550,7 @@ lb_status lb_launch_info(const lb_ctx* c, int* launches, int* blocks, int* threa
     // spheres: their links, and when they move the update, two re-meshing passes and the flags
     const int sph = !c->particles || c->sph.n == 0
                         ? 0
-                        : (c->sph.mass > 0.0 ? 5 + (c->sph.contact_k != 0.0 || c->sph.lub_cut > 0.0 ? 1 : 0) : 1);
+                        : (c->sph.mass > 0.0 ? 4 + (c->sph.contact_k != 0.0 || c->sph.lub_cut > 0.0 ? 1 : 0) : 1);
     if (launches) *launches = (k == LB_KERNEL_TWO_PASS ? 2 : 1) + reflect_launches(c) + sph;
     if (blocks)
         *blocks = k == LB_KERNEL_FUSED ? c->plan.ncols * c->plan.R * c->plan.zsplit

@@ -99,18 +99,6 @@ struct CubeWalk {
     }
 };
 
-// f(u, x, r2, d) for every site of the cube, over the block's threads
-template <typename F>
-__device__ __forceinline__ void for_cube(const Cube& cube, const Geom& g, F&& f) {
-    for (CubeWalk wk(cube, threadIdx.x, blockDim.x); wk.valid(); wk.next()) {
-        int u[3], x[3];
-        cube.site(wk.bx, wk.by, wk.bz, g, u, x);
-        float d[3];
-        const float r2 = cube.dist2(u, d);
-        f(u, x, r2, d);
-    }
-}
-
 // exact minimum-image displacement of grid coordinate x (unwrapped u) from c
 __device__ __forceinline__ double disp(int x, int u, double c, int n) {
     const int m = (x - u) / n;
@@ -515,11 +503,36 @@ __global__ void sphere_update_kernel(Spheres A, Geom g) {
     if (fast) atomicOr(A.err, 2);
 }
 
+// The flags a change of node x (grid coordinates) touches: its own solid
+// bit, and bit j of x + c_j (whose neighbour x + c_j - c_j is x). Set when x
+// becomes solid, cleared when it becomes fluid (a node that changes is never
+// a mask node, and spheres share no node), with atomics since neighbouring
+// changes share words.
+__device__ __forceinline__ void flag_change(uint32_t* __restrict__ flags, const int (&x)[3], uint32_t s,
+                                            bool solid, const Geom& g) {
+    auto apply = [&](uint32_t t, uint32_t bit) {
+        if (solid) atomicOr(flags + t, bit);
+        else atomicAnd(flags + t, ~bit);
+    };
+    apply(s, kSolid);
+    const int xm = wrap_dec(x[0], g.nx), xp = wrap_inc(x[0], g.nx);
+    const int ym = wrap_dec(x[1], g.ny), yp = wrap_inc(x[1], g.ny);
+    const int zm = wrap_dec(x[2], g.nz), zp = wrap_inc(x[2], g.nz);
+    static_for<1, Q>([&](auto J) {
+        constexpr int j = decltype(J)::value;
+        constexpr int cx = Vel<j>::x, cy = Vel<j>::y, cz = Vel<j>::z;
+        const int t3[3] = {cx > 0 ? xp : (cx < 0 ? xm : x[0]), cy > 0 ? yp : (cy < 0 ? ym : x[1]),
+                           cz > 0 ? zp : (cz < 0 ? zm : x[2])};
+        apply(site_of(t3, g), 1u << j);
+    });
+}
+
 // Re-meshing, first pass: nodes sphere q covered and no longer covers become
 // fluid with f^eq(rho0^k, u_b) at the wall velocity there; the sphere loses
 // that momentum (and its moment).
 template <typename S>
-__global__ void __launch_bounds__(kPT) sphere_uncover_kernel(S* __restrict__ st, Spheres A, Geom g, Phys p) {
+__global__ void __launch_bounds__(kPT) sphere_uncover_kernel(S* __restrict__ st, uint32_t* __restrict__ flags,
+                                                            Spheres A, Geom g, Phys p) {
     const int q = blockIdx.x;
     double c[3], v[3], w[3];
     load3(A.r, q, c);
@@ -537,7 +550,6 @@ __global__ void __launch_bounds__(kPT) sphere_uncover_kernel(S* __restrict__ st,
     const float in2 = Rf > sd ? (Rf - sd) * (Rf - sd) : -1.f;
     const float out2 = (Rf + sd) * (Rf + sd);
     const double r0 = (double)p.rho0[0] + (double)p.rho0[1];
-    if (threadIdx.x == 0) A.moved[q] = 0;
     if (within_margin(A, q, g)) return;   // the whole block: no node changed
     __syncthreads();
     double acc[6] = {0, 0, 0, 0, 0, 0};
@@ -548,8 +560,8 @@ __global__ void __launch_bounds__(kPT) sphere_uncover_kernel(S* __restrict__ st,
         if (covered(u, x, r2, c, R2, R2f, g)) return;
         const uint32_t s = site_of(x, g);
         A.owner[s] = 0;
-        A.moved[q] = 1;
         changed = true;
+        flag_change(flags, x, s, false, g);
         const double arm[3] = {disp(x[0], u[0], c[0], g.nx), disp(x[1], u[1], c[1], g.ny),
                                disp(x[2], u[2], c[2], g.nz)};
         double ub[3];
@@ -587,8 +599,9 @@ __global__ void __launch_bounds__(kPT) sphere_uncover_kernel(S* __restrict__ st,
 // populations are cleared. A node held by another sphere or by the mask is
 // an error.
 template <typename S>
-__global__ void __launch_bounds__(kPT) sphere_cover_kernel(S* __restrict__ st, const uint8_t* __restrict__ mask,
-                                                          Spheres A, int absorb, Geom g) {
+__global__ void __launch_bounds__(kPT) sphere_cover_kernel(S* __restrict__ st, uint32_t* __restrict__ flags,
+                                                          const uint8_t* __restrict__ mask, Spheres A, int absorb,
+                                                          Geom g) {
     const int q = blockIdx.x;
     double c[3];
     load3(A.r, q, c);
@@ -617,9 +630,9 @@ __global__ void __launch_bounds__(kPT) sphere_cover_kernel(S* __restrict__ st, c
             atomicOr(A.err, 1);
             return;
         }
-        if (!absorb) return;
-        A.moved[q] = 1;
+        if (!absorb) return;   // a placement: the whole grid's flags follow
         changed = true;
+        flag_change(flags, x, s, true, g);
         double m[3] = {0, 0, 0};
         static_for<1, Q>([&](auto I) {
             constexpr int i = decltype(I)::value;
@@ -669,44 +682,22 @@ __global__ void __launch_bounds__(kPT) sphere_cover_kernel(S* __restrict__ st, c
         }
 }
 
-// Solid flags (bit 0 solid, bit i: x - c_i solid) from the mask and the
-// coverage: over the shell of every moved sphere's widened cube where its
-// re-meshing can have changed a flag, or over the whole grid when
-// whole != 0.
+// Solid flags (bit 0 solid, bit i: x - c_i solid) of the whole grid from the
+// mask and the coverage (after a placement; a re-meshing updates the flags
+// around the nodes it changes itself).
 __global__ void sphere_flags_kernel(uint32_t* __restrict__ flags, const uint8_t* __restrict__ mask, Spheres A,
-                                    int whole, Geom g) {
+                                    Geom g) {
     auto solid = [&](uint32_t s) { return (mask && mask[s]) || A.owner[s] != 0; };
-    auto one = [&](int x, int y, int z) {
-        PullIdx P;
-        pull_indices(g, x, y, z, P);
-        uint32_t f = solid((uint32_t)P.own) ? kSolid : 0u;
-        static_for<1, Q>([&](auto I) {
-            constexpr int i = decltype(I)::value;
-            if (solid((uint32_t)P.src[i])) f |= (1u << i);
-        });
-        flags[P.own] = f;
-    };
-    if (whole) {
-        const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-        if (s >= g.N) return;
-        one((int)(s % g.nx), (int)((s / g.nx) % g.ny), (int)(s / g.plane));
-        return;
-    }
-    const int q = blockIdx.x;
-    if (!A.moved[q]) return;   // no node changed: neither did a flag
-    double c[3];
-    load3(A.r, q, c);
-    const Cube cube(c, A.half + 1);
-    // the changed nodes lie within the step's displacement of the surface
-    // (see the re-meshing), and a flag depends on its node and the 18
-    // neighbours within sqrt 2: the shell within that plus 1.5 of the surface
-    const float Rf = (float)A.radius, sd = A.step[q] + 1e-3f + 1.5f;
-    const float in2 = Rf > sd ? (Rf - sd) * (Rf - sd) : -1.f;
-    const float out2 = (Rf + sd) * (Rf + sd);
-    for_cube(cube, g, [&](const int (&)[3], const int (&x)[3], float r2, const float (&)[3]) {
-        if (r2 < in2 || r2 > out2) return;
-        one(x[0], x[1], x[2]);
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.N) return;
+    PullIdx P;
+    pull_indices(g, (int)(s % g.nx), (int)((s / g.nx) % g.ny), (int)(s / g.plane), P);
+    uint32_t f = solid((uint32_t)P.own) ? kSolid : 0u;
+    static_for<1, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        if (solid((uint32_t)P.src[i])) f |= (1u << i);
     });
+    flags[P.own] = f;
 }
 
 template <typename F32, typename F16, typename BF16>
@@ -745,13 +736,13 @@ cudaError_t launch_sphere_move(int prec, void* state, uint32_t* flags, const uin
     if (e != cudaSuccess) return e;
 #define LBGB_MOVE(T)                                                                  \
     [&] {                                                                             \
-        sphere_uncover_kernel<T><<<S.n, kPT, 0, st>>>((T*)state, S, g, p);            \
-        sphere_cover_kernel<T><<<S.n, kPT, 0, st>>>((T*)state, mask, S, 1, g);        \
+        sphere_uncover_kernel<T><<<S.n, kPT, 0, st>>>((T*)state, flags, S, g, p);            \
+        sphere_cover_kernel<T><<<S.n, kPT, 0, st>>>((T*)state, flags, mask, S, 1, g);        \
     }
-    if ((e = by_prec(prec, LBGB_MOVE(float), LBGB_MOVE(__half), LBGB_MOVE(__nv_bfloat16))) != cudaSuccess) return e;
+    // the two passes update the flags around every node they change
+    e = by_prec(prec, LBGB_MOVE(float), LBGB_MOVE(__half), LBGB_MOVE(__nv_bfloat16));
 #undef LBGB_MOVE
-    sphere_flags_kernel<<<S.n, kPT, 0, st>>>(flags, mask, S, 0, g);
-    return cudaGetLastError();
+    return e;
 }
 
 cudaError_t launch_sphere_place(uint32_t* flags, const uint8_t* mask, const Spheres& S, const Geom& g,
@@ -759,10 +750,10 @@ cudaError_t launch_sphere_place(uint32_t* flags, const uint8_t* mask, const Sphe
     cudaError_t e = cudaMemsetAsync(S.owner, 0, (size_t)g.N * sizeof(int), st);
     if (e != cudaSuccess) return e;
     if (S.n > 0) {
-        sphere_cover_kernel<float><<<S.n, kPT, 0, st>>>(nullptr, mask, S, 0, g);
+        sphere_cover_kernel<float><<<S.n, kPT, 0, st>>>(nullptr, flags, mask, S, 0, g);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    sphere_flags_kernel<<<(unsigned)((g.N + 255) / 256), 256, 0, st>>>(flags, mask, S, 1, g);
+    sphere_flags_kernel<<<(unsigned)((g.N + 255) / 256), 256, 0, st>>>(flags, mask, S, g);
     return cudaGetLastError();
 }
 
