@@ -695,7 +695,8 @@ AsyncPlan plan_fused_async(int nx, int ny, int nz, int sm_count, int prec, bool 
     // resident blocks per SM (half of the SM's shared memory each), take them
     // instead, so that the two blocks' barriers interleave. Measured at 256^3:
     // colour gradient FP16 +0.7 % (with its lean collision; +19 % before),
-    // masked FP16 +1.4 %; unmasked Shan-Chen FP16 -0.2 % and FP32 -3 %,
+    // masked FP16 +5.7 % (colloid mask, re-measured with the lean BGK);
+    // unmasked Shan-Chen FP16 -0.2 % and FP32 -3 %,
     // masked FP32 (two stages each) -4 % (those keep one block of tall
     // tiles).
     if (esize == 2 && box && best.zsplit == 1 && (masked || model == 1)) {
