@@ -690,16 +690,16 @@ AsyncPlan plan_fused_async(int nx, int ny, int nz, int sm_count, int prec, bool 
             if (blocks >= sm_count) break;   // more z-splits only add halo planes
         }
     }
-    // 16-bit storage on masked grids and for the colour gradient (the
-    // heavier per-node work): where short tiles fill exactly one wave of two
-    // resident blocks per SM (half of the SM's shared memory each), take them
-    // instead, so that the two blocks' barriers interleave. Measured at 256^3:
-    // colour gradient FP16 +0.7 % (with its lean collision; +19 % before),
-    // masked FP16 +5.7 % (colloid mask, re-measured with the lean BGK);
-    // unmasked Shan-Chen FP16 -0.2 % and FP32 -3 %,
+    // 16-bit storage on masked grids, for the colour gradient (the heavier
+    // per-node work) and for BF16: where short tiles fill exactly one wave of
+    // two resident blocks per SM (half of the SM's shared memory each), take
+    // them instead, so that the two blocks' barriers interleave. Measured at
+    // 256^3: colour gradient FP16 +0.7 % (with its lean collision; +19 %
+    // before), masked FP16 +5.7 % (colloid mask, with the lean BGK), unmasked
+    // Shan-Chen BF16 +1.1 %; unmasked Shan-Chen FP16 -0.4 %, FP32 -3 % and
     // masked FP32 (two stages each) -4 % (those keep one block of tall
     // tiles).
-    if (esize == 2 && box && best.zsplit == 1 && (masked || model == 1)) {
+    if (esize == 2 && box && best.zsplit == 1 && (masked || model == 1 || prec == 2)) {
         const size_t half_limit = (smem_limit + 1024) / 2 - 1024;
         for (int R = best.R + 1; R <= ny && (long long)ncols * R <= 2LL * sm_count; ++R) {
             if ((long long)ncols * R != 2LL * sm_count) continue;
